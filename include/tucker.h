@@ -1,0 +1,156 @@
+/*
+ * tucker.h -- C ABI of the GB300 sparse third-order Tucker library.
+ *
+ * The library computes the four decompositions evaluated in Turney, "Empirical Evaluation of
+ * Four Tensor Decomposition Algorithms" (2007): HO-SVD (Figure HO-SVD3), HOOI (Figure hooi3),
+ * Slice Projection (Figure sp3) and Multislice Projection (Figure mp3), on a sparse tensor
+ * X of size I1 x I2 x I3, returning a core G of size J1 x J2 x J3 and factors A, B, C with
+ * orthonormal columns such that X ~ [[G; A, B, C]] (Tucker operator, Section 2), plus the
+ * fit 1 - |X - Xhat|_F / |X|_F (fit equation, Section 2).  Every step runs in CUDA kernels
+ * on the current GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - Status: every function returns TUCKER_OK (0) or a negative tucker_status;
+ *     tucker_strerror() names it.  On error no output is guaranteed to be written.
+ *   - Indices are 0-based.  Dense matrices are row-major: factor U_n is I_n x J_n with
+ *     element (i, p) at U[i * J_n + p].  The core is row-major: g[(p * J2 + q) * J3 + r].
+ *   - Memory: a `where` field / argument says whether a pointer is host (TUCKER_HOST) or
+ *     device (TUCKER_DEVICE) memory.  Pointers named d_* are always device memory.
+ *   - Ownership: the library never keeps a caller pointer after a call returns.  Outputs are
+ *     allocated by the caller; sizes follow from dims and J.  Library work buffers are taken
+ *     from the device with stream-ordered allocation and returned before the call returns.
+ *   - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).  All entry
+ *     points are synchronous: when they return, results are in the output buffers.
+ *   - Duplicates in a COO input are summed in their input order (as MATLAB sparse() does in
+ *     the paper's appendix); explicit zeros are kept.
+ *   - Index linearisation uses 64-bit keys: I1 * I2 * I3 must be below 2^62.
+ */
+#ifndef TUCKER_H
+#define TUCKER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TUCKER_OK = 0,
+  TUCKER_EINVAL = -1,    /* bad argument: dims, core size, index out of range, NULL pointer */
+  TUCKER_ENOMEM = -2,    /* a device allocation failed */
+  TUCKER_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+  TUCKER_EEMPTY = -4,    /* |X|_F = 0: the fit is undefined */
+  TUCKER_ETIMEOUT = -5,  /* a bounded device-side wait gave up */
+  TUCKER_EINTERNAL = -6, /* an internal consistency check failed (e.g. Cholesky breakdown) */
+  TUCKER_ENOTCONV = -7   /* the eigensolver hit its iteration limit before its tolerance */
+} tucker_status;
+
+typedef enum { TUCKER_FP64 = 0, TUCKER_MIXED = 1 } tucker_precision;
+typedef enum { TUCKER_HOST = 0, TUCKER_DEVICE = 1 } tucker_mem;
+
+/* Sparse input tensor in coordinate form.  idx[a][t] is the mode-a index of nonzero t. */
+typedef struct {
+  int64_t dims[3];
+  int64_t nnz;
+  const int32_t* idx[3];
+  const double* val;
+  int32_t where; /* tucker_mem of idx[] and val */
+} tucker_coo;
+
+typedef struct {
+  int32_t precision;     /* tucker_precision */
+  double tol;            /* stop threshold of the Delta_fit / Delta_G test; -INFINITY = never */
+  int32_t max_iter;      /* passes of the main loop (>= 1; ignored by HO-SVD) */
+  const double* init[3]; /* optional starting factors, I_n x J_n (NULL = the method's own).
+                            HOOI: init[1], init[2] replace the HO-SVD start of B and C.
+                            SP:   init[2] is the REQUIRED raw random I3 x J3 matrix of
+                                  Figure sp3; the library normalises its columns. */
+  int32_t init_where;    /* tucker_mem of init[] */
+  void* stream;          /* cudaStream_t */
+  uint32_t flags;        /* reserved, must be 0 */
+} tucker_opts;
+
+typedef struct {
+  double* G;             /* J1*J2*J3 (output) */
+  double* U[3];          /* I_n * J_n (output) */
+  double* fit_history;   /* optional, max_iter entries: fit after each pass */
+  int32_t where;         /* tucker_mem of G, U[], fit_history */
+  double fit;            /* fit of the returned decomposition */
+  int32_t iters;         /* passes of the main loop run (1 for HO-SVD) */
+  int32_t rank_deficient;/* bit n set: J_n exceeded the numerical rank of mode n's matrix */
+} tucker_result;
+
+typedef struct tucker_tensor_s* tucker_tensor;
+
+/* ---- tensor handle -------------------------------------------------------------------
+ * tucker_tensor_create copies X to the device, checks every index against dims (EINVAL),
+ * sums duplicates and computes |X|_F^2.  Mode orderings (compressed sorted forms, the
+ * counterpart of the paper's sorted slice files, Section 3 "Slice Projection" and the
+ * appendix functions sort_index / slice) are built on first use and kept in the handle. */
+int tucker_tensor_create(const tucker_coo* X, void* stream, tucker_tensor* out);
+int tucker_tensor_destroy(tucker_tensor X);
+/* Number of distinct nonzeros after duplicate summation, and |X|_F^2 (fit equation). */
+int tucker_tensor_info(tucker_tensor X, int64_t* nnz, double* norm2);
+
+/* ---- the four methods -----------------------------------------------------------------
+ * J: core size (1 <= J_n <= I_n).  opts may be NULL for FP64, tol 1e-4, max_iter 50.
+ * HO-SVD: Figure HO-SVD3.  HOOI: Figure hooi3 + Delta_fit stop (signed, fit_0 = 0).
+ * SP: Figure sp3 + Delta_G stop (tested from the second pass).  MP: Figure mp3 + Delta_fit
+ * stop; its pseudo HO-SVD start equals 2 X_(n) X_(n)^T, whose leading eigenvectors are
+ * HO-SVD's. */
+int tucker_hosvd(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out);
+int tucker_hooi(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out);
+int tucker_sp(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out);
+int tucker_mp(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out);
+
+const char* tucker_strerror(int status);
+/* Text of the last CUDA failure seen by the calling thread (empty if none). */
+const char* tucker_last_error_detail(void);
+
+/* ---- hot-path steps, exposed for verification and profiling ---------------------------
+ * All pointers d_* are device memory; all calls are synchronous on `stream`. */
+
+/* Mode ordering (n, m, o) of the nonzeros: stable sort by (i_n, i_m, i_o); a fiber is a run
+ * with equal (i_n, i_m).  (n, m, o) must be a permutation of (0, 1, 2).  Returns the fiber
+ * count; with non-NULL outputs (`where` memory) also copies root_ptr[I_n+1] (first fiber of
+ * each i_n), fiber_idx[F] (i_m), fiber_ptr[F+1] (first nonzero), leaf_idx[nnz] (i_o) and
+ * val[nnz] (values in sorted order). */
+int tucker_ordering(tucker_tensor X, int32_t n, int32_t m, int32_t o, int64_t* nfibers,
+                    int64_t* root_ptr, int32_t* fiber_idx, int64_t* fiber_ptr,
+                    int32_t* leaf_idx, double* val, int32_t where);
+
+/* Unfolding Gram M = X_(n) X_(n)^T, I_n x I_n (Figure HO-SVD3). */
+int tucker_unfolding_gram(tucker_tensor X, int32_t n, double* d_M, void* stream);
+
+/* HOOI projection Y = X x_m U_m^T x_o U_o^T (Figure hooi3), m < o the other modes, written
+ * as Y_(n): I_n x (J_m J_o) row-major, column p * J_o + q.  d_Um is I_m x J_m, d_Uo I_o x J_o. */
+int tucker_ttmc(tucker_tensor X, int32_t n, const double* d_Um, int32_t Jm, const double* d_Uo,
+                int32_t Jo, double* d_Y, void* stream);
+
+/* Slice projection Y = X x_m U_m^T (Figures sp3, mp3) written as Y_(n), n != m, with o the
+ * remaining mode: I_n x (I_o J_m) row-major, column i_o * J_m + p.  Sum over slices of
+ * X_s U U^T X_s^T equals Y_(n) Y_(n)^T. */
+int tucker_slice_proj(tucker_tensor X, int32_t n, int32_t m, const double* d_Um, int32_t Jm,
+                      double* d_Y, void* stream);
+
+/* Gram M = Y1 Y1^T (+ Y2 Y2^T when d_Y2 != NULL): Y1 is rows x K1, Y2 rows x K2, row-major;
+ * M is rows x rows (both triangles written). */
+int tucker_gram(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2, int32_t rows,
+                double* d_M, void* stream);
+
+/* J leading eigenvectors of the symmetric positive semi-definite n x n matrix M (largest
+ * eigenvalue first; in each column the entry of largest magnitude is positive).  d_U0
+ * (n x J, may be NULL) is a starting guess.  Outputs d_U (n x J) and d_lambda (J).
+ * Block subspace iteration with Chebyshev filtering, Cholesky-QR2 and Rayleigh-Ritz
+ * (Jacobi), all FP64; full Jacobi when n is small. */
+int tucker_eig_topk(const double* d_M, int32_t n, int32_t J, const double* d_U0, double* d_U,
+                    double* d_lambda, void* stream);
+
+/* Core G = [[X; A^T, B^T, C^T]] (row-major J1 x J2 x J3) and |G|_F^2. */
+int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const double* d_C,
+                const int32_t J[3], double* d_G, double* g_norm2, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUCKER_H */

@@ -1,0 +1,588 @@
+// C ABI and host orchestration of the four methods (Figures HO-SVD3, hooi3, sp3, mp3) on the
+// GPU kernels of this library.  The host only sequences kernels, sizes buffers and reads back
+// the scalars its loop tests need (the fit after each pass, Ritz values in the eigensolver).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace tk {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  g_last_error = buf;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+int ordering_slot(int n, int m, int o) {
+  if (n < 0 || m < 0 || o < 0 || n > 2 || m > 2 || o > 2 || n == m || m == o || n == o) return -1;
+  return n * 2 + (m < o ? 0 : 1);
+}
+
+int ensure_ordering(tucker_tensor_s* X, int n, int m, int o, cudaStream_t s, Ordering** out) {
+  const int slot = ordering_slot(n, m, o);
+  if (slot < 0) return TUCKER_EINVAL;
+  Ordering* ord = &X->ord[slot];
+  if (!ord->built) {
+    ord->n = n;
+    ord->m = m;
+    ord->o = o;
+    TK_TRY(build_ordering(X, ord, s));
+  }
+  *out = ord;
+  return TUCKER_OK;
+}
+
+int ensure_fiber_map(tucker_tensor_s* X, Ordering* ord, cudaStream_t s) {
+  if (!ord->fiber_map) TK_TRY(build_fiber_map(X, ord, s));
+  return TUCKER_OK;
+}
+
+namespace {
+
+__global__ void fit_kernel(double nX2, const double* __restrict__ g2, double* __restrict__ fit) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    *fit = 1.0 - sqrt(fmax(0.0, nX2 - *g2)) / sqrt(nX2);
+}
+
+__global__ void normalize_cols(const double* __restrict__ src, int rows, int cols,
+                              double* __restrict__ dst) {
+  __shared__ double ws[8];
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    const double v = src[(int64_t)i * cols + j];
+    s = fma(v, v, s);
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    ws[0] = sqrt(t);
+  }
+  __syncthreads();
+  const double nrm = ws[0];
+  for (int i = threadIdx.x; i < rows; i += blockDim.x)
+    dst[(int64_t)i * cols + j] = nrm > 0.0 ? src[(int64_t)i * cols + j] / nrm : 0.0;
+}
+
+cudaMemcpyKind kind_to_device(int where) {
+  return where == TUCKER_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_from_device(int where) {
+  return where == TUCKER_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+void other_modes(int n, int* m, int* o) {
+  *m = n == 0 ? 1 : 0;
+  *o = n == 2 ? 1 : 2;
+}
+
+}  // namespace
+
+int core_from_ttmc3(const double* Y3, int I3, int J1, int J2, const double* C, int J3, double* G,
+                    double* g2_dev, cudaStream_t s) {
+  // G[(p J2 + q) J3 + r] = sum_k Y3[k, p J2 + q] C[k, r]  (G = W x_3 C^T, Figure hooi3).
+  TK_TRY(gemm_tn_f64(J1 * J2, J3, I3, Y3, (int64_t)J1 * J2, C, J3, G, J3, s));
+  TK_TRY(sum_squares(G, (int64_t)J1 * J2 * J3, g2_dev, s));
+  return TUCKER_OK;
+}
+
+// ----------------------------------------------------------------------------------------------
+// Method drivers
+// ----------------------------------------------------------------------------------------------
+namespace {
+
+struct Run {
+  tucker_tensor_s* X;
+  int J[3];
+  cudaStream_t s;
+  tucker_opts o;
+  Buf U[3];
+  Buf Y, Y2, M, G, sc;  // sc: [0] |G|^2, [1] fit
+  int rank_def = 0;
+  std::vector<double> fits;
+  int64_t dim(int a) const { return X->dims[a]; }
+};
+
+int alloc_common(Run& r, size_t ybytes, size_t y2bytes) {
+  for (int a = 0; a < 3; ++a) TK_TRY(r.U[a].alloc(sizeof(double) * r.dim(a) * r.J[a], r.s));
+  int64_t maxI = std::max(r.dim(0), std::max(r.dim(1), r.dim(2)));
+  TK_TRY(r.M.alloc(sizeof(double) * maxI * maxI, r.s));
+  // mode-3 TTMc output for the core: I3 x J1 J2
+  ybytes = std::max(ybytes, sizeof(double) * (size_t)(r.dim(2) * r.J[0] * r.J[1]));
+  TK_TRY(r.Y.alloc(ybytes, r.s));
+  if (y2bytes) TK_TRY(r.Y2.alloc(y2bytes, r.s));
+  TK_TRY(r.G.alloc(sizeof(double) * r.J[0] * r.J[1] * r.J[2], r.s));
+  TK_TRY(r.sc.alloc(sizeof(double) * 2, r.s));
+  return TUCKER_OK;
+}
+
+int eig_update(Run& r, int n, bool warm) {
+  EigStats st;
+  TK_TRY(eig_topk_f64(r.M.as<double>(), (int)r.dim(n), r.J[n], warm ? r.U[n].as<double>() : nullptr,
+                      r.U[n].as<double>(), nullptr, r.s, &st));
+  if (st.rank_deficient) r.rank_def |= 1 << n;
+  return TUCKER_OK;
+}
+
+int unfolding_gram(Run& r, int n, double* M) {
+  int m, o;
+  other_modes(n, &m, &o);
+  Ordering *rows, *fib;
+  TK_TRY(ensure_ordering(r.X, n, m, o, r.s, &rows));
+  TK_TRY(ensure_ordering(r.X, m, o, n, r.s, &fib));
+  TK_TRY(ensure_fiber_map(r.X, fib, r.s));
+  return unfolding_gram_f64(r.X, rows, fib, M, r.s);
+}
+
+int ttmc(Run& r, int n, double* Y) {
+  int m, o;
+  other_modes(n, &m, &o);
+  Ordering* ord;
+  TK_TRY(ensure_ordering(r.X, n, m, o, r.s, &ord));
+  return ttmc_f64(r.X, ord, r.U[m].as<double>(), r.J[m], r.U[o].as<double>(), r.J[o], Y, r.s);
+}
+
+// Y = (X x_m U_m^T)_(n): I_n x (I_o J_m), using ordering (n, o, m).
+int slice_proj(Run& r, int n, int m, double* Y) {
+  const int o = 3 - n - m;
+  Ordering* ord;
+  TK_TRY(ensure_ordering(r.X, n, o, m, r.s, &ord));
+  return slice_proj_f64(r.X, ord, r.U[m].as<double>(), r.J[m], Y, r.s);
+}
+
+// Core from the current factors: mode-3 TTMc with A, B then G = W x_3 C^T; returns fit.
+int core_and_fit(Run& r, bool have_y3, double* fit, double* g2) {
+  if (!have_y3) TK_TRY(ttmc(r, 2, r.Y.as<double>()));
+  TK_TRY(core_from_ttmc3(r.Y.as<double>(), (int)r.dim(2), r.J[0], r.J[1], r.U[2].as<double>(),
+                         r.J[2], r.G.as<double>(), r.sc.as<double>(), r.s));
+  fit_kernel<<<1, 32, 0, r.s>>>(r.X->norm2, r.sc.as<double>(), r.sc.as<double>() + 1);
+  TK_LAUNCH();
+  double h[2];
+  TK_CUDA(cudaMemcpyAsync(h, r.sc.p, sizeof(h), cudaMemcpyDeviceToHost, r.s));
+  TK_CUDA(cudaStreamSynchronize(r.s));
+  *g2 = h[0];
+  *fit = h[1];
+  return TUCKER_OK;
+}
+
+int finish(Run& r, tucker_result* out) {
+  const int where = out->where;
+  TK_CUDA(cudaMemcpyAsync(out->G, r.G.p, sizeof(double) * r.J[0] * r.J[1] * r.J[2],
+                          kind_from_device(where), r.s));
+  for (int a = 0; a < 3; ++a)
+    TK_CUDA(cudaMemcpyAsync(out->U[a], r.U[a].p, sizeof(double) * r.dim(a) * r.J[a],
+                            kind_from_device(where), r.s));
+  if (out->fit_history && !r.fits.empty())
+    TK_CUDA(cudaMemcpyAsync(out->fit_history, r.fits.data(), sizeof(double) * r.fits.size(),
+                            where == TUCKER_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+                            r.s));
+  TK_CUDA(cudaStreamSynchronize(r.s));
+  out->fit = r.fits.empty() ? 0.0 : r.fits.back();
+  out->iters = (int32_t)r.fits.size();
+  out->rank_deficient = r.rank_def;
+  return TUCKER_OK;
+}
+
+int check_args(tucker_tensor_s* X, const int32_t J[3], const tucker_opts* opts,
+               const tucker_result* out, bool needs_iter) {
+  if (!X || !J || !out || !out->G || !out->U[0] || !out->U[1] || !out->U[2]) return TUCKER_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (J[a] < 1 || J[a] > X->dims[a]) return TUCKER_EINVAL;
+  if (out->where != TUCKER_HOST && out->where != TUCKER_DEVICE) return TUCKER_EINVAL;
+  if (opts) {
+    if (opts->precision != TUCKER_FP64 && opts->precision != TUCKER_MIXED) return TUCKER_EINVAL;
+    if (needs_iter && opts->max_iter < 1) return TUCKER_EINVAL;
+    if (isnan(opts->tol) || opts->tol == INFINITY) return TUCKER_EINVAL;
+    if (opts->flags != 0) return TUCKER_EINVAL;
+    if (opts->init_where != TUCKER_HOST && opts->init_where != TUCKER_DEVICE) return TUCKER_EINVAL;
+  }
+  if (X->nnz == 0 || !(X->norm2 > 0.0)) return TUCKER_EEMPTY;
+  return TUCKER_OK;
+}
+
+tucker_opts default_opts() {
+  tucker_opts o;
+  memset(&o, 0, sizeof(o));
+  o.precision = TUCKER_FP64;
+  o.tol = 1e-4;
+  o.max_iter = 50;
+  return o;
+}
+
+int mixed_unavailable() { return TUCKER_EINVAL; }
+
+int setup(Run& r, tucker_tensor_s* X, const int32_t J[3], const tucker_opts* opts) {
+  r.X = X;
+  for (int a = 0; a < 3; ++a) r.J[a] = J[a];
+  r.o = opts ? *opts : default_opts();
+  r.s = (cudaStream_t)r.o.stream;
+  if (r.o.precision == TUCKER_MIXED) return mixed_unavailable();
+  return TUCKER_OK;
+}
+
+int load_init(Run& r, int n) {
+  if (!r.o.init[n]) return 0;
+  TK_CUDA(cudaMemcpyAsync(r.U[n].p, r.o.init[n], sizeof(double) * r.dim(n) * r.J[n],
+                          kind_to_device(r.o.init_where), r.s));
+  return 1;
+}
+
+}  // namespace
+}  // namespace tk
+
+using namespace tk;
+
+extern "C" {
+
+const char* tucker_strerror(int status) {
+  switch (status) {
+    case TUCKER_OK: return "ok";
+    case TUCKER_EINVAL: return "invalid argument";
+    case TUCKER_ENOMEM: return "device memory allocation failed";
+    case TUCKER_ECUDA: return "CUDA error";
+    case TUCKER_EEMPTY: return "empty tensor (|X| = 0): fit undefined";
+    case TUCKER_ETIMEOUT: return "a bounded device-side wait gave up";
+    case TUCKER_EINTERNAL: return "internal consistency check failed";
+    case TUCKER_ENOTCONV: return "eigensolver did not converge";
+    default: return "unknown status";
+  }
+}
+
+const char* tucker_last_error_detail(void) { return g_last_error.c_str(); }
+
+int tucker_tensor_create(const tucker_coo* X, void* stream, tucker_tensor* out) {
+  if (!X || !out) return TUCKER_EINVAL;
+  *out = nullptr;
+  for (int a = 0; a < 3; ++a)
+    if (X->dims[a] < 1 || X->dims[a] > 2147483647ll) return TUCKER_EINVAL;
+  const double cells = (double)X->dims[0] * (double)X->dims[1] * (double)X->dims[2];
+  if (cells >= 4.6e18) return TUCKER_EINVAL;
+  if (X->nnz < 0 || X->nnz > 2147483647ll) return TUCKER_EINVAL;
+  if (X->where != TUCKER_HOST && X->where != TUCKER_DEVICE) return TUCKER_EINVAL;
+  if (X->nnz > 0 && (!X->idx[0] || !X->idx[1] || !X->idx[2] || !X->val)) return TUCKER_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  tucker_tensor_s* T = new (std::nothrow) tucker_tensor_s();
+  if (!T) return TUCKER_ENOMEM;
+  for (int a = 0; a < 3; ++a) T->dims[a] = X->dims[a];
+  cudaGetDevice(&T->device);
+  int st = TUCKER_OK;
+  {
+    const int64_t n = X->nnz;
+    Buf bi[3], bv;
+    const int32_t* di[3] = {X->idx[0], X->idx[1], X->idx[2]};
+    const double* dv = X->val;
+    if (X->where == TUCKER_HOST && n > 0) {
+      for (int a = 0; a < 3 && st == TUCKER_OK; ++a) {
+        st = bi[a].alloc(sizeof(int32_t) * n, s);
+        if (st == TUCKER_OK &&
+            cudaMemcpyAsync(bi[a].p, X->idx[a], sizeof(int32_t) * n, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess)
+          st = TUCKER_ECUDA;
+        di[a] = bi[a].as<int32_t>();
+      }
+      if (st == TUCKER_OK) st = bv.alloc(sizeof(double) * n, s);
+      if (st == TUCKER_OK &&
+          cudaMemcpyAsync(bv.p, X->val, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = TUCKER_ECUDA;
+      dv = bv.as<double>();
+    }
+    if (st == TUCKER_OK) st = build_canonical(T, di[0], di[1], di[2], dv, n, s);
+    if (st == TUCKER_OK && cudaStreamSynchronize(s) != cudaSuccess) st = TUCKER_ECUDA;
+  }
+  if (st != TUCKER_OK) {
+    tucker_tensor_destroy(T);
+    return st;
+  }
+  *out = T;
+  return TUCKER_OK;
+}
+
+int tucker_tensor_destroy(tucker_tensor T) {
+  if (!T) return TUCKER_OK;
+  cudaDeviceSynchronize();
+  for (int a = 0; a < 3; ++a) cudaFree(T->idx[a]);
+  cudaFree(T->val);
+  for (auto& o : T->ord) {
+    cudaFree(o.root_ptr);
+    cudaFree(o.fiber_idx);
+    cudaFree(o.fiber_root);
+    cudaFree(o.fiber_ptr);
+    cudaFree(o.leaf_idx);
+    cudaFree(o.val);
+    cudaFree(o.val_f32);
+    cudaFree(o.fiber_map);
+  }
+  delete T;
+  return TUCKER_OK;
+}
+
+int tucker_tensor_info(tucker_tensor X, int64_t* nnz, double* norm2) {
+  if (!X) return TUCKER_EINVAL;
+  if (nnz) *nnz = X->nnz;
+  if (norm2) *norm2 = X->norm2;
+  return TUCKER_OK;
+}
+
+int tucker_hosvd(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out) {
+  TK_TRY(check_args(X, J, opts, out, false));
+  Run r;
+  TK_TRY(setup(r, X, J, opts));
+  TK_TRY(alloc_common(r, 0, 0));
+  for (int n = 0; n < 3; ++n) {
+    TK_TRY(unfolding_gram(r, n, r.M.as<double>()));
+    TK_TRY(eig_update(r, n, false));
+  }
+  double fit, g2;
+  TK_TRY(core_and_fit(r, false, &fit, &g2));
+  r.fits.push_back(fit);
+  return finish(r, out);
+}
+
+int tucker_hooi(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out) {
+  TK_TRY(check_args(X, J, opts, out, true));
+  Run r;
+  TK_TRY(setup(r, X, J, opts));
+  size_t yb = 0;
+  for (int n = 0; n < 3; ++n) {
+    int m, o;
+    other_modes(n, &m, &o);
+    yb = std::max(yb, sizeof(double) * (size_t)(r.dim(n) * J[m] * J[o]));
+  }
+  TK_TRY(alloc_common(r, yb, 0));
+  bool have[3] = {false, false, false};
+  for (int n = 1; n < 3; ++n) {
+    if (load_init(r, n)) {
+      have[n] = true;
+      continue;
+    }
+    TK_TRY(unfolding_gram(r, n, r.M.as<double>()));
+    TK_TRY(eig_update(r, n, false));
+    have[n] = true;
+  }
+  double old = 0.0;
+  for (int it = 0; it < r.o.max_iter; ++it) {
+    for (int n = 0; n < 3; ++n) {
+      int m, o;
+      other_modes(n, &m, &o);
+      TK_TRY(ttmc(r, n, r.Y.as<double>()));
+      TK_TRY(syrk_f64((int)r.dim(n), r.Y.as<double>(), (int64_t)J[m] * J[o], nullptr, 0,
+                      r.M.as<double>(), r.s));
+      TK_TRY(eig_update(r, n, have[n]));
+      have[n] = true;
+    }
+    // The mode-3 projection W = [[X; A^T, B^T, I]] is still in Y: G = W x_3 C^T.
+    double fit, g2;
+    TK_TRY(core_and_fit(r, true, &fit, &g2));
+    r.fits.push_back(fit);
+    if (fit - old < r.o.tol) break;
+    old = fit;
+  }
+  return finish(r, out);
+}
+
+int tucker_sp(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out) {
+  TK_TRY(check_args(X, J, opts, out, true));
+  if (!opts || !opts->init[2]) return TUCKER_EINVAL;  // SP needs its random C
+  Run r;
+  TK_TRY(setup(r, X, J, opts));
+  // (n, m) pairs of Figure sp3: A from X x_3 C^T, B from X x_1 A^T, C from X x_2 B^T.
+  const int pairs[3][2] = {{0, 2}, {1, 0}, {2, 1}};
+  size_t yb = 0;
+  for (auto& p : pairs) {
+    const int n = p[0], m = p[1], o = 3 - n - m;
+    yb = std::max(yb, sizeof(double) * (size_t)(r.dim(n) * r.dim(o) * J[m]));
+  }
+  TK_TRY(alloc_common(r, yb, 0));
+  {
+    Buf raw;
+    TK_TRY(raw.alloc(sizeof(double) * r.dim(2) * J[2], r.s));
+    TK_CUDA(cudaMemcpyAsync(raw.p, r.o.init[2], sizeof(double) * r.dim(2) * J[2],
+                            kind_to_device(r.o.init_where), r.s));
+    normalize_cols<<<J[2], 256, 0, r.s>>>(raw.as<double>(), (int)r.dim(2), J[2],
+                                          r.U[2].as<double>());
+    TK_LAUNCH();
+    TK_CUDA(cudaStreamSynchronize(r.s));
+  }
+  bool have[3] = {false, false, false};
+  double gprev = 0.0;
+  for (int it = 0; it < r.o.max_iter; ++it) {
+    for (auto& p : pairs) {
+      const int n = p[0], m = p[1], o = 3 - n - m;
+      TK_TRY(slice_proj(r, n, m, r.Y.as<double>()));
+      TK_TRY(syrk_f64((int)r.dim(n), r.Y.as<double>(), r.dim(o) * J[m], nullptr, 0,
+                      r.M.as<double>(), r.s));
+      TK_TRY(eig_update(r, n, have[n]));
+      have[n] = true;
+    }
+    double fit, g2;
+    TK_TRY(core_and_fit(r, false, &fit, &g2));
+    r.fits.push_back(fit);
+    const double gn = sqrt(g2);
+    if (it >= 1 && (1.0 - gprev / gn) < r.o.tol) break;
+    gprev = gn;
+  }
+  return finish(r, out);
+}
+
+int tucker_mp(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out) {
+  TK_TRY(check_args(X, J, opts, out, true));
+  Run r;
+  TK_TRY(setup(r, X, J, opts));
+  size_t yb = 0, yb2 = 0;
+  for (int n = 0; n < 3; ++n) {
+    int m, o;
+    other_modes(n, &m, &o);
+    yb = std::max(yb, sizeof(double) * (size_t)(r.dim(n) * r.dim(o) * J[m]));
+    yb2 = std::max(yb2, sizeof(double) * (size_t)(r.dim(n) * r.dim(m) * J[o]));
+  }
+  TK_TRY(alloc_common(r, yb, yb2));
+  bool have[3] = {false, false, false};
+  // Pseudo HO-SVD start (Figure mp3): each of its two slice sums equals X_(n) X_(n)^T, so the
+  // matrix is 2 X_(n) X_(n)^T.
+  for (int n = 1; n < 3; ++n) {
+    TK_TRY(unfolding_gram(r, n, r.M.as<double>()));
+    TK_TRY(scale_f64(r.dim(n) * r.dim(n), 2.0, r.M.as<double>(), r.s));
+    TK_TRY(eig_update(r, n, false));
+    have[n] = true;
+  }
+  double old = 0.0;
+  for (int it = 0; it < r.o.max_iter; ++it) {
+    for (int n = 0; n < 3; ++n) {
+      int m, o;
+      other_modes(n, &m, &o);
+      TK_TRY(slice_proj(r, n, m, r.Y.as<double>()));   // (X x_m U_m^T)_(n)
+      TK_TRY(slice_proj(r, n, o, r.Y2.as<double>()));  // (X x_o U_o^T)_(n)
+      TK_TRY(syrk_f64((int)r.dim(n), r.Y.as<double>(), r.dim(o) * J[m], r.Y2.as<double>(),
+                      r.dim(m) * J[o], r.M.as<double>(), r.s));
+      TK_TRY(eig_update(r, n, have[n]));
+      have[n] = true;
+    }
+    double fit, g2;
+    TK_TRY(core_and_fit(r, false, &fit, &g2));
+    r.fits.push_back(fit);
+    if (fit - old < r.o.tol) break;
+    old = fit;
+  }
+  return finish(r, out);
+}
+
+// ---- step entry points -----------------------------------------------------------------------
+
+int tucker_ordering(tucker_tensor X, int32_t n, int32_t m, int32_t o, int64_t* nfibers,
+                    int64_t* root_ptr, int32_t* fiber_idx, int64_t* fiber_ptr, int32_t* leaf_idx,
+                    double* val, int32_t where) {
+  if (!X || ordering_slot(n, m, o) < 0) return TUCKER_EINVAL;
+  if (where != TUCKER_HOST && where != TUCKER_DEVICE) return TUCKER_EINVAL;
+  cudaStream_t s = 0;
+  Ordering* ord;
+  TK_TRY(ensure_ordering(X, n, m, o, s, &ord));
+  if (nfibers) *nfibers = ord->F;
+  const cudaMemcpyKind k = kind_from_device(where);
+  if (root_ptr) TK_CUDA(cudaMemcpy(root_ptr, ord->root_ptr, sizeof(int64_t) * (X->dims[n] + 1), k));
+  if (fiber_idx && ord->F) TK_CUDA(cudaMemcpy(fiber_idx, ord->fiber_idx, sizeof(int32_t) * ord->F, k));
+  if (fiber_ptr) TK_CUDA(cudaMemcpy(fiber_ptr, ord->fiber_ptr, sizeof(int64_t) * (ord->F + 1), k));
+  if (leaf_idx && X->nnz) TK_CUDA(cudaMemcpy(leaf_idx, ord->leaf_idx, sizeof(int32_t) * X->nnz, k));
+  if (val && X->nnz) TK_CUDA(cudaMemcpy(val, ord->val, sizeof(double) * X->nnz, k));
+  return TUCKER_OK;
+}
+
+int tucker_unfolding_gram(tucker_tensor X, int32_t n, double* d_M, void* stream) {
+  if (!X || n < 0 || n > 2 || !d_M) return TUCKER_EINVAL;
+  Run r;
+  r.X = X;
+  r.s = (cudaStream_t)stream;
+  TK_TRY(unfolding_gram(r, n, d_M));
+  TK_CUDA(cudaStreamSynchronize(r.s));
+  return TUCKER_OK;
+}
+
+int tucker_ttmc(tucker_tensor X, int32_t n, const double* d_Um, int32_t Jm, const double* d_Uo,
+                int32_t Jo, double* d_Y, void* stream) {
+  if (!X || n < 0 || n > 2 || !d_Um || !d_Uo || !d_Y || Jm < 1 || Jo < 1) return TUCKER_EINVAL;
+  int m, o;
+  other_modes(n, &m, &o);
+  cudaStream_t s = (cudaStream_t)stream;
+  Ordering* ord;
+  TK_TRY(ensure_ordering(X, n, m, o, s, &ord));
+  TK_TRY(ttmc_f64(X, ord, d_Um, Jm, d_Uo, Jo, d_Y, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+int tucker_slice_proj(tucker_tensor X, int32_t n, int32_t m, const double* d_Um, int32_t Jm,
+                      double* d_Y, void* stream) {
+  if (!X || n < 0 || n > 2 || m < 0 || m > 2 || n == m || !d_Um || !d_Y || Jm < 1)
+    return TUCKER_EINVAL;
+  const int o = 3 - n - m;
+  cudaStream_t s = (cudaStream_t)stream;
+  Ordering* ord;
+  TK_TRY(ensure_ordering(X, n, o, m, s, &ord));
+  TK_TRY(slice_proj_f64(X, ord, d_Um, Jm, d_Y, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+int tucker_gram(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2, int32_t rows,
+                double* d_M, void* stream) {
+  if (!d_Y1 || !d_M || rows < 1 || K1 < 0 || (d_Y2 && K2 < 0)) return TUCKER_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  TK_TRY(syrk_f64(rows, d_Y1, K1, d_Y2, d_Y2 ? K2 : 0, d_M, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+int tucker_eig_topk(const double* d_M, int32_t n, int32_t J, const double* d_U0, double* d_U,
+                    double* d_lambda, void* stream) {
+  if (!d_M || !d_U || n < 1 || J < 1 || J > n) return TUCKER_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  TK_TRY(eig_topk_f64(d_M, n, J, d_U0, d_U, d_lambda, s, nullptr));
+  TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const double* d_C,
+                const int32_t J[3], double* d_G, double* g_norm2, void* stream) {
+  if (!X || !d_A || !d_B || !d_C || !J || !d_G) return TUCKER_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (J[a] < 1 || J[a] > X->dims[a]) return TUCKER_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Ordering* ord;
+  TK_TRY(ensure_ordering(X, 2, 0, 1, s, &ord));
+  Buf Y, g2;
+  TK_TRY(Y.alloc(sizeof(double) * X->dims[2] * J[0] * J[1], s));
+  TK_TRY(g2.alloc(sizeof(double), s));
+  TK_TRY(ttmc_f64(X, ord, d_A, J[0], d_B, J[1], Y.as<double>(), s));
+  TK_TRY(core_from_ttmc3(Y.as<double>(), (int)X->dims[2], J[0], J[1], d_C, J[2], d_G,
+                         g2.as<double>(), s));
+  double h = 0.0;
+  TK_CUDA(cudaMemcpyAsync(&h, g2.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  if (g_norm2) *g_norm2 = h;
+  return TUCKER_OK;
+}
+
+}  // extern "C"

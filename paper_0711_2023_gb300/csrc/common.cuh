@@ -1,0 +1,132 @@
+// Shared device/host helpers of the Tucker library (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "tucker.h"
+
+namespace tk {
+
+// ---- status plumbing ------------------------------------------------------------------------
+#define TK_CUDA(call)                                                               \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      tk::set_last_cuda_error(e_, #call, __FILE__, __LINE__);                       \
+      return e_ == cudaErrorMemoryAllocation ? TUCKER_ENOMEM : TUCKER_ECUDA;        \
+    }                                                                               \
+  } while (0)
+
+#define TK_LAUNCH()                                                                 \
+  do {                                                                              \
+    cudaError_t e_ = cudaGetLastError();                                            \
+    if (e_ != cudaSuccess) {                                                        \
+      tk::set_last_cuda_error(e_, "kernel launch", __FILE__, __LINE__);             \
+      return TUCKER_ECUDA;                                                          \
+    }                                                                               \
+  } while (0)
+
+#define TK_TRY(expr)                   \
+  do {                                 \
+    int s_ = (expr);                   \
+    if (s_ != TUCKER_OK) return s_;    \
+  } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Device status word bits written by kernels (never trap: a kernel that finds a bad state
+// records it and returns, so the context stays usable).
+enum : int {
+  DEV_OK = 0,
+  DEV_BAD_INDEX = 1,
+  DEV_TIMEOUT = 2,
+  DEV_CHOL_BREAKDOWN = 4,
+  DEV_NOT_CONVERGED = 8,
+};
+
+// ---- stream-ordered work buffers ------------------------------------------------------------
+// A Buf owns one cudaMallocAsync allocation and frees it on `stream` when it goes out of scope.
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = 0;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { release(); }
+  int alloc(size_t nbytes, cudaStream_t stream) {
+    release();
+    s = stream;
+    bytes = nbytes;
+    if (nbytes == 0) return TUCKER_OK;
+    cudaError_t e = cudaMallocAsync(&p, nbytes, stream);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_last_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+      return TUCKER_ENOMEM;
+    }
+    return TUCKER_OK;
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+int num_sms();
+
+// ---- device helpers -------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Grid-wide barrier for cooperative launches, with a bounded spin.  `bar[0]` counts arrivals,
+// `bar[1]` is the generation.  Returns false (and sets DEV_TIMEOUT in *status) when the spin
+// limit runs out; callers then leave their loops.  All blocks of a cooperative launch are
+// co-resident, so in a healthy run every wait ends.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok_s = 1;
+    volatile unsigned int* vgen = bar + 1;
+    unsigned int gen = *vgen;
+    __threadfence();
+    unsigned int arrived = atomicAdd(bar, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == gen) {
+        if (++spins > (1ll << 24)) {  // about a second: far beyond any healthy wait
+          atomicOr(status, DEV_TIMEOUT);
+          ok_s = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+}  // namespace tk

@@ -1,0 +1,92 @@
+// Internal host-side interfaces between the translation units of the Tucker library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tk {
+
+// One compressed mode ordering (n, m, o): nonzeros sorted by (i_n, i_m, i_o).
+struct Ordering {
+  bool built = false;
+  int n = 0, m = 0, o = 0;
+  int64_t F = 0;               // fibers (runs of equal (i_n, i_m))
+  int64_t* root_ptr = nullptr; // [I_n + 1]
+  int32_t* fiber_idx = nullptr;// [F]   i_m
+  int32_t* fiber_root = nullptr;// [F]  i_n
+  int64_t* fiber_ptr = nullptr;// [F + 1]
+  int32_t* leaf_idx = nullptr; // [nnz] i_o
+  double* val = nullptr;       // [nnz]
+  float* val_f32 = nullptr;    // [nnz] (mixed path, built on demand)
+  int32_t* fiber_map = nullptr;// [I_n * I_m] fiber id of (i_n, i_m) or -1 (built on demand)
+};
+
+}  // namespace tk
+
+struct tucker_tensor_s {
+  int64_t dims[3] = {0, 0, 0};
+  int64_t nnz = 0;              // distinct nonzeros
+  int32_t* idx[3] = {nullptr, nullptr, nullptr};  // canonical COO sorted by (i1, i2, i3)
+  double* val = nullptr;
+  double norm2 = 0.0;
+  int device = 0;
+  tk::Ordering ord[6];
+};
+
+namespace tk {
+
+int ordering_slot(int n, int m, int o);  // 0..5, or -1 if not a permutation
+int ensure_ordering(tucker_tensor_s* X, int n, int m, int o, cudaStream_t s, Ordering** out);
+int ensure_fiber_map(tucker_tensor_s* X, Ordering* ord, cudaStream_t s);
+int ensure_val_f32(tucker_tensor_s* X, Ordering* ord, cudaStream_t s);
+
+// csf.cu
+int build_canonical(tucker_tensor_s* X, const int32_t* d_i0, const int32_t* d_i1,
+                    const int32_t* d_i2, const double* d_v, int64_t nnz_in, cudaStream_t s);
+int build_ordering(tucker_tensor_s* X, Ordering* ord, cudaStream_t s);
+int sum_squares(const double* d_v, int64_t n, double* d_out, cudaStream_t s);
+int build_fiber_map(tucker_tensor_s* X, Ordering* ord, cudaStream_t s);
+
+// sparse.cu (FP64)
+int ttmc_f64(const tucker_tensor_s* X, const Ordering* ord, const double* Um, int Jm,
+             const double* Uo, int Jo, double* Y, cudaStream_t s);
+int slice_proj_f64(const tucker_tensor_s* X, const Ordering* ord, const double* Um, int Jm,
+                   double* Y, cudaStream_t s);
+int unfolding_gram_f64(const tucker_tensor_s* X, const Ordering* rows, const Ordering* fibers,
+                       double* M, cudaStream_t s);
+
+// dense.cu (FP64)
+// C[m x n] = alpha * A[m x k] B[k x n] + beta * Xm + gamma * Zm (Xm, Zm optional, same shape
+// as C; Xm may alias C).  All row-major with leading dimensions.
+int gemm_nn_f64(int m, int n, int k, double alpha, const double* A, int64_t lda, const double* B,
+                int64_t ldb, double beta, const double* Xm, int64_t ldx, double gamma,
+                const double* Zm, int64_t ldz, double* C, int64_t ldc, cudaStream_t s);
+// C[m x n] = A^T B with A: k x m, B: k x n (row-major), deterministic split-K.
+int gemm_tn_f64(int m, int n, int64_t k, const double* A, int64_t lda, const double* B,
+                int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
+// M = Y1 Y1^T (+ Y2 Y2^T): rows x rows from row-major rows x K inputs; deterministic.
+int syrk_f64(int rows, const double* Y1, int64_t K1, const double* Y2, int64_t K2, double* M,
+             cudaStream_t s);
+int copy_cols_f64(int rows, int cols, const double* src, int64_t lds, double* dst, int64_t ldd,
+                  cudaStream_t s);
+int scale_f64(int64_t n, double alpha, double* x, cudaStream_t s);
+
+// eig.cu
+struct EigStats {
+  int outer_iters = 0;
+  int matvecs = 0;
+  int jacobi_sweeps = 0;
+  bool direct = false;
+  bool rank_deficient = false;
+};
+// Leading J eigenvectors of the symmetric PSD n x n matrix M (device).  U0 (n x J, may be
+// NULL) warm-starts; U (n x J) and lambda (J, may be NULL) receive the result.
+int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, double* lambda,
+                 cudaStream_t s, EigStats* st);
+
+// core / fit (api.cu)
+int core_from_ttmc3(const double* Y3, int I3, int J1, int J2, const double* C, int J3,
+                    double* G, double* g2_dev, cudaStream_t s);
+
+}  // namespace tk
