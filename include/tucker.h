@@ -138,6 +138,29 @@ int tucker_slice_proj(tucker_tensor X, int32_t n, int32_t m, const double* d_Um,
 int tucker_gram(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2, int32_t rows,
                 double* d_M, void* stream);
 
+/* ---- mixed-precision steps (TUCKER_MIXED form) ---------------------------------------------
+ * BF16 matrices are passed as uint16_t bit patterns.  A "split" matrix Y is stored as two
+ * BF16 matrices hi = bf16(y), lo = bf16(y - hi), row-major with row stride ld (elements, a
+ * multiple of 64, columns K..ld-1 zero), base addresses 16-byte aligned. */
+
+/* tucker_ttmc in FP32 from FP32 factors: writes the split Y_(n) (rows I_n, K = J_m J_o, stride
+ * ldY) when d_Yhi/d_Ylo are given, and/or the FP32 Y_(n) (stride J_m J_o) when d_Y32 is. */
+int tucker_ttmc_mixed(tucker_tensor X, int32_t n, const float* d_Um, int32_t Jm,
+                      const float* d_Uo, int32_t Jo, uint16_t* d_Yhi, uint16_t* d_Ylo,
+                      int64_t ldY, float* d_Y32, void* stream);
+
+/* tucker_slice_proj in FP32 from an FP32 factor, written split (K = I_o J_m, stride ldY). */
+int tucker_slice_proj_mixed(tucker_tensor X, int32_t n, int32_t m, const float* d_Um, int32_t Jm,
+                            uint16_t* d_Yhi, uint16_t* d_Ylo, int64_t ldY, void* stream);
+
+/* Gram M = Y1 Y1^T (+ Y2 Y2^T) of split matrices on the tensor cores: each product is
+ * hi hi^T + hi lo^T + lo hi^T in BF16 with FP32 accumulation over K chunks of at most 4096,
+ * chunks summed in FP64.  M (rows x rows, FP64) is exactly symmetric.  Pass d_Y2hi = NULL for
+ * one term.  ETIMEOUT if a bounded wait inside the kernel gave up. */
+int tucker_gram_bf16x3(const uint16_t* d_Y1hi, const uint16_t* d_Y1lo, int64_t K1, int64_t ld1,
+                       const uint16_t* d_Y2hi, const uint16_t* d_Y2lo, int64_t K2, int64_t ld2,
+                       int32_t rows, double* d_M, void* stream);
+
 /* J leading eigenvectors of the symmetric positive semi-definite n x n matrix M (largest
  * eigenvalue first; in each column the entry of largest magnitude is positive).  d_U0
  * (n x J, may be NULL) is a starting guess.  Outputs d_U (n x J) and d_lambda (J).
@@ -149,6 +172,19 @@ int tucker_eig_topk(const double* d_M, int32_t n, int32_t J, const double* d_U0,
 /* Core G = [[X; A^T, B^T, C^T]] (row-major J1 x J2 x J3) and |G|_F^2. */
 int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const double* d_C,
                 const int32_t J[3], double* d_G, double* g_norm2, void* stream);
+
+/* ---- profiling (no counterpart in the paper; the paper reports wall time only) ----------
+ * tucker_profile_enable(1) clears previous records and starts recording CUDA events on the
+ * launching stream around the hot-path kernels; 0 stops.  tucker_profile_query sums, for the
+ * kernel `name` ("syrk_f64", "ttmc_f64", "slice_proj_f64", "unfold_gram_f64", "gemm_nn_f64",
+ * "jacobi_f64", "csf_build"), the launches recorded, their device time in milliseconds and
+ * their algorithmic FLOPs and bytes (what the method must compute and move, not what the
+ * kernel happens to do).  tucker_launch_count returns the number of kernels this library has
+ * launched in the process. */
+void tucker_profile_enable(int on);
+int tucker_profile_query(const char* name, int64_t* launches, double* total_ms, double* flops,
+                         double* bytes);
+int64_t tucker_launch_count(void);
 
 #ifdef __cplusplus
 }

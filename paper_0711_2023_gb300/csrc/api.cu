@@ -1,6 +1,12 @@
 // C ABI and host orchestration of the four methods (Figures HO-SVD3, hooi3, sp3, mp3) on the
 // GPU kernels of this library.  The host only sequences kernels, sizes buffers and reads back
 // the scalars its loop tests need (the fit after each pass, Ritz values in the eigensolver).
+//
+// Two precision forms share one driver:
+//   FP64   every step in FP64 (CUDA cores);
+//   MIXED  projections in FP32 from FP32 factors, written as BF16 hi/lo pairs; the Gram on the
+//          tensor cores (BF16x3, FP32 accumulation per K chunk, FP64 chunk sum); the
+//          eigensolver (Cholesky-QR2, Rayleigh-Ritz), the core and the fit in FP64.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -22,6 +28,8 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
   snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
   g_last_error = buf;
 }
+
+void set_error_detail(const char* msg) { g_last_error = msg; }
 
 int num_sms() {
   static int n = 0;
@@ -111,33 +119,83 @@ int core_from_ttmc3(const double* Y3, int I3, int J1, int J2, const double* C, i
 }
 
 // ----------------------------------------------------------------------------------------------
-// Method drivers
+// Method driver
 // ----------------------------------------------------------------------------------------------
 namespace {
 
+enum class Method { HOSVD, HOOI, SP, MP };
+
+// (n, m) pairs of Figure sp3: A from X x_3 C^T, B from X x_1 A^T, C from X x_2 B^T.
+const int SP_PAIRS[3][2] = {{0, 2}, {1, 0}, {2, 1}};
+
 struct Run {
-  tucker_tensor_s* X;
-  int J[3];
-  cudaStream_t s;
+  tucker_tensor_s* X = nullptr;
+  Method method = Method::HOOI;
+  int J[3] = {0, 0, 0};
+  cudaStream_t s = 0;
   tucker_opts o;
-  Buf U[3];
-  Buf Y, Y2, M, G, sc;  // sc: [0] |G|^2, [1] fit
+  bool mixed = false;
+  Buf U[3], U32[3];
+  Buf Y, Y2;                  // FP64 projections; Y also stages the core input
+  Buf Yh, Yl, Y2h, Y2l, Y32;  // mixed projections
+  Buf M, G, sc;               // sc: [0] |G|^2, [1] fit
   int rank_def = 0;
   std::vector<double> fits;
   int64_t dim(int a) const { return X->dims[a]; }
 };
 
-int alloc_common(Run& r, size_t ybytes, size_t y2bytes) {
-  for (int a = 0; a < 3; ++a) TK_TRY(r.U[a].alloc(sizeof(double) * r.dim(a) * r.J[a], r.s));
-  int64_t maxI = std::max(r.dim(0), std::max(r.dim(1), r.dim(2)));
+size_t bf16_bytes(int64_t rows, int64_t K) { return 2 * (size_t)rows * (size_t)gram_ld(K); }
+
+int alloc_buffers(Run& r) {
+  const int* J = r.J;
+  for (int a = 0; a < 3; ++a) {
+    TK_TRY(r.U[a].alloc(sizeof(double) * r.dim(a) * J[a], r.s));
+    if (r.mixed) TK_TRY(r.U32[a].alloc(sizeof(float) * r.dim(a) * J[a], r.s));
+  }
+  const int64_t maxI = std::max(r.dim(0), std::max(r.dim(1), r.dim(2)));
   TK_TRY(r.M.alloc(sizeof(double) * maxI * maxI, r.s));
-  // mode-3 TTMc output for the core: I3 x J1 J2
-  ybytes = std::max(ybytes, sizeof(double) * (size_t)(r.dim(2) * r.J[0] * r.J[1]));
-  TK_TRY(r.Y.alloc(ybytes, r.s));
-  if (y2bytes) TK_TRY(r.Y2.alloc(y2bytes, r.s));
-  TK_TRY(r.G.alloc(sizeof(double) * r.J[0] * r.J[1] * r.J[2], r.s));
+  TK_TRY(r.G.alloc(sizeof(double) * J[0] * J[1] * J[2], r.s));
   TK_TRY(r.sc.alloc(sizeof(double) * 2, r.s));
+  const size_t core_in = (size_t)(r.dim(2) * J[0] * J[1]);  // W_(3): I3 x J1 J2
+  size_t y = core_in * sizeof(double), y2 = 0, yb = 0, yb2 = 0;
+  for (int n = 0; n < 3; ++n) {
+    int m, o;
+    other_modes(n, &m, &o);
+    if (r.method == Method::HOOI) {
+      y = std::max(y, sizeof(double) * (size_t)(r.dim(n) * J[m] * J[o]));
+      yb = std::max(yb, bf16_bytes(r.dim(n), (int64_t)J[m] * J[o]));
+    } else if (r.method == Method::SP) {
+      const int nn = SP_PAIRS[n][0], mm = SP_PAIRS[n][1], oo = 3 - nn - mm;
+      y = std::max(y, sizeof(double) * (size_t)(r.dim(nn) * r.dim(oo) * J[mm]));
+      yb = std::max(yb, bf16_bytes(r.dim(nn), r.dim(oo) * J[mm]));
+    } else if (r.method == Method::MP) {
+      y = std::max(y, sizeof(double) * (size_t)(r.dim(n) * r.dim(o) * J[m]));
+      y2 = std::max(y2, sizeof(double) * (size_t)(r.dim(n) * r.dim(m) * J[o]));
+      yb = std::max(yb, bf16_bytes(r.dim(n), r.dim(o) * J[m]));
+      yb2 = std::max(yb2, bf16_bytes(r.dim(n), r.dim(m) * J[o]));
+    }
+  }
+  if (r.mixed) {
+    TK_TRY(r.Y.alloc(core_in * sizeof(double), r.s));
+    TK_TRY(r.Y32.alloc(core_in * sizeof(float), r.s));
+    if (yb) {
+      TK_TRY(r.Yh.alloc(yb / 2, r.s));
+      TK_TRY(r.Yl.alloc(yb / 2, r.s));
+    }
+    if (yb2) {
+      TK_TRY(r.Y2h.alloc(yb2 / 2, r.s));
+      TK_TRY(r.Y2l.alloc(yb2 / 2, r.s));
+    }
+  } else {
+    TK_TRY(r.Y.alloc(y, r.s));
+    if (y2) TK_TRY(r.Y2.alloc(y2, r.s));
+  }
   return TUCKER_OK;
+}
+
+int refresh32(Run& r, int n) {
+  if (!r.mixed) return TUCKER_OK;
+  return f64_to_f32(r.U[n].as<double>(), r.U32[n].as<float>(), r.dim(n) * r.J[n], r.s);
 }
 
 int eig_update(Run& r, int n, bool warm) {
@@ -145,7 +203,7 @@ int eig_update(Run& r, int n, bool warm) {
   TK_TRY(eig_topk_f64(r.M.as<double>(), (int)r.dim(n), r.J[n], warm ? r.U[n].as<double>() : nullptr,
                       r.U[n].as<double>(), nullptr, r.s, &st));
   if (st.rank_deficient) r.rank_def |= 1 << n;
-  return TUCKER_OK;
+  return refresh32(r, n);
 }
 
 int unfolding_gram(Run& r, int n, double* M) {
@@ -158,25 +216,80 @@ int unfolding_gram(Run& r, int n, double* M) {
   return unfolding_gram_f64(r.X, rows, fib, M, r.s);
 }
 
-int ttmc(Run& r, int n, double* Y) {
+int ordering(Run& r, int n, int m, int o, Ordering** ord) {
+  TK_TRY(ensure_ordering(r.X, n, m, o, r.s, ord));
+  if (r.mixed) TK_TRY(ensure_val_f32(r.X, *ord, r.s));
+  return TUCKER_OK;
+}
+
+// Mode-n matrix of HOOI (Figure hooi3): Gram of (X x_m U_m^T x_o U_o^T)_(n).  For n = 2 the
+// projection W is kept for the core.
+int hooi_matrix(Run& r, int n) {
   int m, o;
   other_modes(n, &m, &o);
   Ordering* ord;
-  TK_TRY(ensure_ordering(r.X, n, m, o, r.s, &ord));
-  return ttmc_f64(r.X, ord, r.U[m].as<double>(), r.J[m], r.U[o].as<double>(), r.J[o], Y, r.s);
+  TK_TRY(ordering(r, n, m, o, &ord));
+  const int64_t K = (int64_t)r.J[m] * r.J[o];
+  if (!r.mixed) {
+    TK_TRY(ttmc_f64(r.X, ord, r.U[m].as<double>(), r.J[m], r.U[o].as<double>(), r.J[o],
+                    r.Y.as<double>(), r.s));
+    return syrk_f64((int)r.dim(n), r.Y.as<double>(), K, nullptr, 0, r.M.as<double>(), r.s);
+  }
+  const int64_t ld = gram_ld(K);
+  __nv_bfloat16 *yh = r.Yh.as<__nv_bfloat16>(), *yl = r.Yl.as<__nv_bfloat16>();
+  TK_TRY(ttmc_mixed(r.X, ord, r.U32[m].as<float>(), r.J[m], r.U32[o].as<float>(), r.J[o], yh, yl,
+                    ld, n == 2 ? r.Y32.as<float>() : nullptr, r.s));
+  GramTerm t{yh, yl, K, ld};
+  return gram_bf16x3((int)r.dim(n), 1, &t, r.M.as<double>(), r.s);
 }
 
-// Y = (X x_m U_m^T)_(n): I_n x (I_o J_m), using ordering (n, o, m).
-int slice_proj(Run& r, int n, int m, double* Y) {
+// One slice-projection term (X x_m U_m^T)_(n), on ordering (n, o, m); K = I_o J_m.
+int slice_term(Run& r, int n, int m, int which, GramTerm* t) {
   const int o = 3 - n - m;
   Ordering* ord;
-  TK_TRY(ensure_ordering(r.X, n, o, m, r.s, &ord));
-  return slice_proj_f64(r.X, ord, r.U[m].as<double>(), r.J[m], Y, r.s);
+  TK_TRY(ordering(r, n, o, m, &ord));
+  const int64_t K = r.dim(o) * r.J[m];
+  if (!r.mixed) {
+    double* Y = which == 0 ? r.Y.as<double>() : r.Y2.as<double>();
+    TK_TRY(slice_proj_f64(r.X, ord, r.U[m].as<double>(), r.J[m], Y, r.s));
+    *t = GramTerm{nullptr, nullptr, K, K};
+    return TUCKER_OK;
+  }
+  const int64_t ld = gram_ld(K);
+  __nv_bfloat16* yh = which == 0 ? r.Yh.as<__nv_bfloat16>() : r.Y2h.as<__nv_bfloat16>();
+  __nv_bfloat16* yl = which == 0 ? r.Yl.as<__nv_bfloat16>() : r.Y2l.as<__nv_bfloat16>();
+  TK_TRY(slice_proj_mixed(r.X, ord, r.U32[m].as<float>(), r.J[m], yh, yl, ld, r.s));
+  *t = GramTerm{yh, yl, K, ld};
+  return TUCKER_OK;
 }
 
-// Core from the current factors: mode-3 TTMc with A, B then G = W x_3 C^T; returns fit.
-int core_and_fit(Run& r, bool have_y3, double* fit, double* g2) {
-  if (!have_y3) TK_TRY(ttmc(r, 2, r.Y.as<double>()));
+// Mode-n matrix of SP (one term, Figure sp3) or MP (two terms, Figure mp3).
+int slice_matrix(Run& r, int n, int m1, int m2) {
+  GramTerm t[2];
+  TK_TRY(slice_term(r, n, m1, 0, &t[0]));
+  const int nt = m2 >= 0 ? 2 : 1;
+  if (nt == 2) TK_TRY(slice_term(r, n, m2, 1, &t[1]));
+  if (!r.mixed)
+    return syrk_f64((int)r.dim(n), r.Y.as<double>(), t[0].K, nt == 2 ? r.Y2.as<double>() : nullptr,
+                    nt == 2 ? t[1].K : 0, r.M.as<double>(), r.s);
+  return gram_bf16x3((int)r.dim(n), nt, t, r.M.as<double>(), r.s);
+}
+
+// G = [[X; A^T, B^T, C^T]] from W = [[X; A^T, B^T, I]] (computed unless w_ready), then the fit.
+int core_and_fit(Run& r, bool w_ready, double* fit, double* g2) {
+  Ordering* ord;
+  TK_TRY(ordering(r, 2, 0, 1, &ord));
+  const int64_t nW = r.dim(2) * r.J[0] * r.J[1];
+  if (!r.mixed) {
+    if (!w_ready)
+      TK_TRY(ttmc_f64(r.X, ord, r.U[0].as<double>(), r.J[0], r.U[1].as<double>(), r.J[1],
+                      r.Y.as<double>(), r.s));
+  } else {
+    if (!w_ready)
+      TK_TRY(ttmc_mixed(r.X, ord, r.U32[0].as<float>(), r.J[0], r.U32[1].as<float>(), r.J[1],
+                        nullptr, nullptr, 0, r.Y32.as<float>(), r.s));
+    TK_TRY(f32_to_f64(r.Y32.as<float>(), r.Y.as<double>(), nW, r.s));
+  }
   TK_TRY(core_from_ttmc3(r.Y.as<double>(), (int)r.dim(2), r.J[0], r.J[1], r.U[2].as<double>(),
                          r.J[2], r.G.as<double>(), r.sc.as<double>(), r.s));
   fit_kernel<<<1, 32, 0, r.s>>>(r.X->norm2, r.sc.as<double>(), r.sc.as<double>() + 1);
@@ -233,22 +346,100 @@ tucker_opts default_opts() {
   return o;
 }
 
-int mixed_unavailable() { return TUCKER_EINVAL; }
+int load_init(Run& r, int n) {
+  if (!r.o.init[n]) return 0;
+  if (cudaMemcpyAsync(r.U[n].p, r.o.init[n], sizeof(double) * r.dim(n) * r.J[n],
+                      kind_to_device(r.o.init_where), r.s) != cudaSuccess)
+    return -1;
+  return refresh32(r, n) == TUCKER_OK ? 1 : -1;
+}
 
-int setup(Run& r, tucker_tensor_s* X, const int32_t J[3], const tucker_opts* opts) {
+int run_method(Method method, tucker_tensor_s* X, const int32_t J[3], const tucker_opts* opts,
+               tucker_result* out) {
+  TK_TRY(check_args(X, J, opts, out, method != Method::HOSVD));
+  if (method == Method::SP && (!opts || !opts->init[2])) return TUCKER_EINVAL;  // random C
+  Run r;
   r.X = X;
+  r.method = method;
   for (int a = 0; a < 3; ++a) r.J[a] = J[a];
   r.o = opts ? *opts : default_opts();
   r.s = (cudaStream_t)r.o.stream;
-  if (r.o.precision == TUCKER_MIXED) return mixed_unavailable();
-  return TUCKER_OK;
-}
+  r.mixed = r.o.precision == TUCKER_MIXED;
+  TK_TRY(alloc_buffers(r));
+  bool have[3] = {false, false, false};
 
-int load_init(Run& r, int n) {
-  if (!r.o.init[n]) return 0;
-  TK_CUDA(cudaMemcpyAsync(r.U[n].p, r.o.init[n], sizeof(double) * r.dim(n) * r.J[n],
-                          kind_to_device(r.o.init_where), r.s));
-  return 1;
+  // ---- initialisation -------------------------------------------------------------------
+  if (method == Method::HOSVD) {
+    for (int n = 0; n < 3; ++n) {
+      TK_TRY(unfolding_gram(r, n, r.M.as<double>()));
+      TK_TRY(eig_update(r, n, false));
+    }
+    double fit, g2;
+    TK_TRY(core_and_fit(r, false, &fit, &g2));
+    r.fits.push_back(fit);
+    return finish(r, out);
+  }
+  if (method == Method::SP) {
+    // Figure sp3: C is a random I3 x J3 matrix with its columns normalised.
+    Buf raw;
+    TK_TRY(raw.alloc(sizeof(double) * r.dim(2) * J[2], r.s));
+    TK_CUDA(cudaMemcpyAsync(raw.p, r.o.init[2], sizeof(double) * r.dim(2) * J[2],
+                            kind_to_device(r.o.init_where), r.s));
+    normalize_cols<<<J[2], 256, 0, r.s>>>(raw.as<double>(), (int)r.dim(2), J[2],
+                                          r.U[2].as<double>());
+    TK_LAUNCH();
+    TK_TRY(refresh32(r, 2));
+    TK_CUDA(cudaStreamSynchronize(r.s));
+  } else {
+    // HOOI: B, C from HO-SVD (or given).  MP: pseudo HO-SVD; each of its two slice sums equals
+    // X_(n) X_(n)^T (Figure mp3), so the matrix is 2 X_(n) X_(n)^T.
+    for (int n = 1; n < 3; ++n) {
+      if (method == Method::HOOI) {
+        const int li = load_init(r, n);
+        if (li < 0) return TUCKER_ECUDA;
+        if (li > 0) {
+          have[n] = true;
+          continue;
+        }
+      }
+      TK_TRY(unfolding_gram(r, n, r.M.as<double>()));
+      if (method == Method::MP) TK_TRY(scale_f64(r.dim(n) * r.dim(n), 2.0, r.M.as<double>(), r.s));
+      TK_TRY(eig_update(r, n, false));
+      have[n] = true;
+    }
+  }
+
+  // ---- main loop ------------------------------------------------------------------------
+  double old = 0.0, gprev = 0.0;
+  for (int it = 0; it < r.o.max_iter; ++it) {
+    for (int step = 0; step < 3; ++step) {
+      int n = step;
+      if (method == Method::HOOI) {
+        TK_TRY(hooi_matrix(r, n));
+      } else if (method == Method::SP) {
+        n = SP_PAIRS[step][0];
+        TK_TRY(slice_matrix(r, n, SP_PAIRS[step][1], -1));
+      } else {
+        int m, o;
+        other_modes(n, &m, &o);
+        TK_TRY(slice_matrix(r, n, m, o));
+      }
+      TK_TRY(eig_update(r, n, have[n]));
+      have[n] = true;
+    }
+    double fit, g2;
+    TK_TRY(core_and_fit(r, method == Method::HOOI, &fit, &g2));
+    r.fits.push_back(fit);
+    if (method == Method::SP) {
+      const double gn = sqrt(g2);
+      if (it >= 1 && (1.0 - gprev / gn) < r.o.tol) break;  // Delta_G test
+      gprev = gn;
+    } else {
+      if (fit - old < r.o.tol) break;                      // Delta_fit test (signed)
+      old = fit;
+    }
+  }
+  return finish(r, out);
 }
 
 }  // namespace
@@ -348,146 +539,16 @@ int tucker_tensor_info(tucker_tensor X, int64_t* nnz, double* norm2) {
 }
 
 int tucker_hosvd(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out) {
-  TK_TRY(check_args(X, J, opts, out, false));
-  Run r;
-  TK_TRY(setup(r, X, J, opts));
-  TK_TRY(alloc_common(r, 0, 0));
-  for (int n = 0; n < 3; ++n) {
-    TK_TRY(unfolding_gram(r, n, r.M.as<double>()));
-    TK_TRY(eig_update(r, n, false));
-  }
-  double fit, g2;
-  TK_TRY(core_and_fit(r, false, &fit, &g2));
-  r.fits.push_back(fit);
-  return finish(r, out);
+  return run_method(Method::HOSVD, X, J, opts, out);
 }
-
 int tucker_hooi(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out) {
-  TK_TRY(check_args(X, J, opts, out, true));
-  Run r;
-  TK_TRY(setup(r, X, J, opts));
-  size_t yb = 0;
-  for (int n = 0; n < 3; ++n) {
-    int m, o;
-    other_modes(n, &m, &o);
-    yb = std::max(yb, sizeof(double) * (size_t)(r.dim(n) * J[m] * J[o]));
-  }
-  TK_TRY(alloc_common(r, yb, 0));
-  bool have[3] = {false, false, false};
-  for (int n = 1; n < 3; ++n) {
-    if (load_init(r, n)) {
-      have[n] = true;
-      continue;
-    }
-    TK_TRY(unfolding_gram(r, n, r.M.as<double>()));
-    TK_TRY(eig_update(r, n, false));
-    have[n] = true;
-  }
-  double old = 0.0;
-  for (int it = 0; it < r.o.max_iter; ++it) {
-    for (int n = 0; n < 3; ++n) {
-      int m, o;
-      other_modes(n, &m, &o);
-      TK_TRY(ttmc(r, n, r.Y.as<double>()));
-      TK_TRY(syrk_f64((int)r.dim(n), r.Y.as<double>(), (int64_t)J[m] * J[o], nullptr, 0,
-                      r.M.as<double>(), r.s));
-      TK_TRY(eig_update(r, n, have[n]));
-      have[n] = true;
-    }
-    // The mode-3 projection W = [[X; A^T, B^T, I]] is still in Y: G = W x_3 C^T.
-    double fit, g2;
-    TK_TRY(core_and_fit(r, true, &fit, &g2));
-    r.fits.push_back(fit);
-    if (fit - old < r.o.tol) break;
-    old = fit;
-  }
-  return finish(r, out);
+  return run_method(Method::HOOI, X, J, opts, out);
 }
-
 int tucker_sp(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out) {
-  TK_TRY(check_args(X, J, opts, out, true));
-  if (!opts || !opts->init[2]) return TUCKER_EINVAL;  // SP needs its random C
-  Run r;
-  TK_TRY(setup(r, X, J, opts));
-  // (n, m) pairs of Figure sp3: A from X x_3 C^T, B from X x_1 A^T, C from X x_2 B^T.
-  const int pairs[3][2] = {{0, 2}, {1, 0}, {2, 1}};
-  size_t yb = 0;
-  for (auto& p : pairs) {
-    const int n = p[0], m = p[1], o = 3 - n - m;
-    yb = std::max(yb, sizeof(double) * (size_t)(r.dim(n) * r.dim(o) * J[m]));
-  }
-  TK_TRY(alloc_common(r, yb, 0));
-  {
-    Buf raw;
-    TK_TRY(raw.alloc(sizeof(double) * r.dim(2) * J[2], r.s));
-    TK_CUDA(cudaMemcpyAsync(raw.p, r.o.init[2], sizeof(double) * r.dim(2) * J[2],
-                            kind_to_device(r.o.init_where), r.s));
-    normalize_cols<<<J[2], 256, 0, r.s>>>(raw.as<double>(), (int)r.dim(2), J[2],
-                                          r.U[2].as<double>());
-    TK_LAUNCH();
-    TK_CUDA(cudaStreamSynchronize(r.s));
-  }
-  bool have[3] = {false, false, false};
-  double gprev = 0.0;
-  for (int it = 0; it < r.o.max_iter; ++it) {
-    for (auto& p : pairs) {
-      const int n = p[0], m = p[1], o = 3 - n - m;
-      TK_TRY(slice_proj(r, n, m, r.Y.as<double>()));
-      TK_TRY(syrk_f64((int)r.dim(n), r.Y.as<double>(), r.dim(o) * J[m], nullptr, 0,
-                      r.M.as<double>(), r.s));
-      TK_TRY(eig_update(r, n, have[n]));
-      have[n] = true;
-    }
-    double fit, g2;
-    TK_TRY(core_and_fit(r, false, &fit, &g2));
-    r.fits.push_back(fit);
-    const double gn = sqrt(g2);
-    if (it >= 1 && (1.0 - gprev / gn) < r.o.tol) break;
-    gprev = gn;
-  }
-  return finish(r, out);
+  return run_method(Method::SP, X, J, opts, out);
 }
-
 int tucker_mp(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out) {
-  TK_TRY(check_args(X, J, opts, out, true));
-  Run r;
-  TK_TRY(setup(r, X, J, opts));
-  size_t yb = 0, yb2 = 0;
-  for (int n = 0; n < 3; ++n) {
-    int m, o;
-    other_modes(n, &m, &o);
-    yb = std::max(yb, sizeof(double) * (size_t)(r.dim(n) * r.dim(o) * J[m]));
-    yb2 = std::max(yb2, sizeof(double) * (size_t)(r.dim(n) * r.dim(m) * J[o]));
-  }
-  TK_TRY(alloc_common(r, yb, yb2));
-  bool have[3] = {false, false, false};
-  // Pseudo HO-SVD start (Figure mp3): each of its two slice sums equals X_(n) X_(n)^T, so the
-  // matrix is 2 X_(n) X_(n)^T.
-  for (int n = 1; n < 3; ++n) {
-    TK_TRY(unfolding_gram(r, n, r.M.as<double>()));
-    TK_TRY(scale_f64(r.dim(n) * r.dim(n), 2.0, r.M.as<double>(), r.s));
-    TK_TRY(eig_update(r, n, false));
-    have[n] = true;
-  }
-  double old = 0.0;
-  for (int it = 0; it < r.o.max_iter; ++it) {
-    for (int n = 0; n < 3; ++n) {
-      int m, o;
-      other_modes(n, &m, &o);
-      TK_TRY(slice_proj(r, n, m, r.Y.as<double>()));   // (X x_m U_m^T)_(n)
-      TK_TRY(slice_proj(r, n, o, r.Y2.as<double>()));  // (X x_o U_o^T)_(n)
-      TK_TRY(syrk_f64((int)r.dim(n), r.Y.as<double>(), r.dim(o) * J[m], r.Y2.as<double>(),
-                      r.dim(m) * J[o], r.M.as<double>(), r.s));
-      TK_TRY(eig_update(r, n, have[n]));
-      have[n] = true;
-    }
-    double fit, g2;
-    TK_TRY(core_and_fit(r, false, &fit, &g2));
-    r.fits.push_back(fit);
-    if (fit - old < r.o.tol) break;
-    old = fit;
-  }
-  return finish(r, out);
+  return run_method(Method::MP, X, J, opts, out);
 }
 
 // ---- step entry points -----------------------------------------------------------------------
@@ -551,6 +612,55 @@ int tucker_gram(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2, 
   if (!d_Y1 || !d_M || rows < 1 || K1 < 0 || (d_Y2 && K2 < 0)) return TUCKER_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   TK_TRY(syrk_f64(rows, d_Y1, K1, d_Y2, d_Y2 ? K2 : 0, d_M, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+int tucker_ttmc_mixed(tucker_tensor X, int32_t n, const float* d_Um, int32_t Jm, const float* d_Uo,
+                      int32_t Jo, uint16_t* d_Yhi, uint16_t* d_Ylo, int64_t ldY, float* d_Y32,
+                      void* stream) {
+  if (!X || n < 0 || n > 2 || !d_Um || !d_Uo || Jm < 1 || Jo < 1) return TUCKER_EINVAL;
+  if ((!d_Yhi) != (!d_Ylo) || (!d_Yhi && !d_Y32)) return TUCKER_EINVAL;
+  if (d_Yhi && (ldY < (int64_t)Jm * Jo || ldY % 64 != 0)) return TUCKER_EINVAL;
+  int m, o;
+  other_modes(n, &m, &o);
+  cudaStream_t s = (cudaStream_t)stream;
+  Ordering* ord;
+  TK_TRY(ensure_ordering(X, n, m, o, s, &ord));
+  TK_TRY(ensure_val_f32(X, ord, s));
+  TK_TRY(ttmc_mixed(X, ord, d_Um, Jm, d_Uo, Jo, (__nv_bfloat16*)d_Yhi, (__nv_bfloat16*)d_Ylo, ldY,
+                    d_Y32, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+int tucker_slice_proj_mixed(tucker_tensor X, int32_t n, int32_t m, const float* d_Um, int32_t Jm,
+                            uint16_t* d_Yhi, uint16_t* d_Ylo, int64_t ldY, void* stream) {
+  if (!X || n < 0 || n > 2 || m < 0 || m > 2 || n == m || !d_Um || !d_Yhi || !d_Ylo || Jm < 1)
+    return TUCKER_EINVAL;
+  const int o = 3 - n - m;
+  if (ldY < X->dims[o] * Jm || ldY % 64 != 0) return TUCKER_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Ordering* ord;
+  TK_TRY(ensure_ordering(X, n, o, m, s, &ord));
+  TK_TRY(ensure_val_f32(X, ord, s));
+  TK_TRY(slice_proj_mixed(X, ord, d_Um, Jm, (__nv_bfloat16*)d_Yhi, (__nv_bfloat16*)d_Ylo, ldY, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+int tucker_gram_bf16x3(const uint16_t* d_Y1hi, const uint16_t* d_Y1lo, int64_t K1, int64_t ld1,
+                       const uint16_t* d_Y2hi, const uint16_t* d_Y2lo, int64_t K2, int64_t ld2,
+                       int32_t rows, double* d_M, void* stream) {
+  if (!d_Y1hi || !d_Y1lo || !d_M || rows < 1 || K1 < 1 || ld1 < K1 || ld1 % 64) return TUCKER_EINVAL;
+  const bool two = d_Y2hi != nullptr;
+  if (two && (!d_Y2lo || K2 < 1 || ld2 < K2 || ld2 % 64)) return TUCKER_EINVAL;
+  const uintptr_t al = (uintptr_t)d_Y1hi | (uintptr_t)d_Y1lo | (uintptr_t)d_Y2hi | (uintptr_t)d_Y2lo;
+  if (al % 16) return TUCKER_EINVAL;  // TMA needs 16-byte aligned bases
+  GramTerm t[2] = {{(const __nv_bfloat16*)d_Y1hi, (const __nv_bfloat16*)d_Y1lo, K1, ld1},
+                   {(const __nv_bfloat16*)d_Y2hi, (const __nv_bfloat16*)d_Y2lo, K2, ld2}};
+  cudaStream_t s = (cudaStream_t)stream;
+  TK_TRY(gram_bf16x3(rows, two ? 2 : 1, t, d_M, s));
   TK_CUDA(cudaStreamSynchronize(s));
   return TUCKER_OK;
 }

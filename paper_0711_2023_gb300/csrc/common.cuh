@@ -20,6 +20,7 @@ namespace tk {
 
 #define TK_LAUNCH()                                                                 \
   do {                                                                              \
+    tk::count_launch();                                                             \
     cudaError_t e_ = cudaGetLastError();                                            \
     if (e_ != cudaSuccess) {                                                        \
       tk::set_last_cuda_error(e_, "kernel launch", __FILE__, __LINE__);             \
@@ -34,6 +35,25 @@ namespace tk {
   } while (0)
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void set_error_detail(const char* msg);
+void count_launch();
+
+// Records CUDA events around its lifetime on `s` when profiling is enabled
+// (tucker_profile_enable), tagged with the launch's algorithmic FLOPs and bytes.
+class ProfScope {
+ public:
+  ProfScope(const char* name, cudaStream_t s, double flops, double bytes);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  double flops_, bytes_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+  bool active_ = false;
+};
 
 // Device status word bits written by kernels (never trap: a kernel that finds a bad state
 // records it and returns, so the context stays usable).

@@ -347,6 +347,7 @@ int sum_squares(const double* d_v, int64_t n, double* d_out, cudaStream_t s) {
 int build_canonical(tucker_tensor_s* X, const int32_t* d_i0, const int32_t* d_i1,
                     const int32_t* d_i2, const double* d_v, int64_t n, cudaStream_t s) {
   const int64_t d0 = X->dims[0], d1 = X->dims[1], d2 = X->dims[2];
+  ProfScope prof("csf_build", s, 0.0, 20.0 * n + 20.0 * n);
   Buf k0, k1, v0, v1, head, uid, stat, tot;
   TK_TRY(k0.alloc(8 * (size_t)n, s));
   TK_TRY(k1.alloc(8 * (size_t)n, s));
@@ -401,6 +402,7 @@ int build_ordering(tucker_tensor_s* X, Ordering* ord, cudaStream_t s) {
   const int n = ord->n, m = ord->m, o = ord->o;
   const int64_t nnz = X->nnz;
   const int64_t dn = X->dims[n], dm = X->dims[m], dd = X->dims[o];
+  ProfScope prof("csf_build", s, 0.0, 20.0 * nnz + 12.0 * nnz);
   Buf k0, k1, v0, v1, head, fid, tot;
   const size_t nn = (size_t)(nnz ? nnz : 1);
   TK_TRY(k0.alloc(8 * nn, s));

@@ -226,6 +226,8 @@ int gemm_nn_f64(int m, int n, int k, double alpha, const double* A, int64_t lda,
                 int64_t ldb, double beta, const double* Xm, int64_t ldx, double gamma,
                 const double* Zm, int64_t ldz, double* C, int64_t ldc, cudaStream_t s) {
   if (m <= 0 || n <= 0) return TUCKER_OK;
+  ProfScope prof("gemm_nn_f64", s, 2.0 * m * n * (double)k,
+                 8.0 * ((double)m * k + (double)k * n + (double)m * n));
   dim3 grid(ceil_div(n, BN), ceil_div(m, BM));
   gemm_nn_kernel<<<grid, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, Xm, ldx, gamma, Zm,
                                       ldz, C, ldc);
@@ -257,6 +259,8 @@ int syrk_f64(int rows, const double* Y1, int64_t K1, const double* Y2, int64_t K
              cudaStream_t s) {
   if (rows <= 0) return TUCKER_OK;
   if (!Y2) K2 = 0;
+  ProfScope prof("syrk_f64", s, (double)rows * (rows + 1) * (double)(K1 + K2),
+                 8.0 * rows * (double)(K1 + K2) + 8.0 * rows * rows);
   const int nt = ceil_div(rows, BM);
   const int npairs = nt * (nt + 1) / 2;
   const int64_t K = K1 + K2;

@@ -280,10 +280,27 @@ __global__ void residual_norms(const double* __restrict__ W, const double* __res
   }
 }
 
-__global__ void scale_cols(double* V, int64_t ld, int n, int cols, const double* __restrict__ sc) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n * cols) return;
-  V[(t / cols) * ld + (t % cols)] *= sc[t % cols];
+// Scales every column of V (n x cols, ld) to unit 2-norm (zero columns are left alone).
+// One block per column.
+__global__ void normalize_cols_inplace(double* V, int64_t ld, int n) {
+  __shared__ double ws[8];
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = V[(int64_t)i * ld + j];
+    s = fma(v, v, s);
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    ws[0] = t > 0.0 ? 1.0 / sqrt(t) : 1.0;
+  }
+  __syncthreads();
+  const double inv = ws[0];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) V[(int64_t)i * ld + j] *= inv;
 }
 
 // Columns [c0, c1) of V (n x ld) from a counter-based hash: uniform in [-1, 1).
@@ -362,7 +379,11 @@ int jacobi_eig(const double* A, int mreal, int64_t lda, double* Qout, double* ev
   const int work = std::max(h * (h + 1) / 2, m * h);
   const int grid = cooperative_grid(std::min(work, 1 << 22), smem);
   void* args[] = {&g};
-  TK_CUDA(cudaLaunchCooperativeKernel((void*)jacobi_kernel, grid, 256, args, smem, s));
+  {
+    ProfScope prof("jacobi_f64", s, 0.0, 0.0);
+    count_launch();
+    TK_CUDA(cudaLaunchCooperativeKernel((void*)jacobi_kernel, grid, 256, args, smem, s));
+  }
   rank_desc<<<ceil_div(mreal, 256), 256, 0, s>>>(ev.as<double>(), mreal, ord.as<int>());
   TK_LAUNCH();
   permute_cols<<<ceil_div((int64_t)mreal * mreal, 256), 256, 0, s>>>(
@@ -385,7 +406,7 @@ namespace {
 int cholqr2(double* V, int64_t ldv, int n, int k, double* T, double* Gk, double* R, double* Ri,
             int* dstat, cudaStream_t s) {
   int clean = 0;
-  for (int pass = 0; pass < 5 && clean < 2; ++pass) {
+  for (int pass = 0; pass < 8 && clean < 2; ++pass) {
     TK_TRY(gemm_tn_f64(k, k, n, V, ldv, V, ldv, Gk, k, s));
     double shift = 0.0;
     bool shifted = false;
@@ -453,7 +474,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
 
   const double tol = 3e-13;
   const int max_outer = 120, dmax = 24;
-  const double growth_cap = 1e4;
+  const double growth_cap = 1e4, abs_cap = 1e8;
   Buf Vb, T1, T2, T3, H, Qh, evh, Gk, R, Ri, P, rn, stat;
   const size_t nk = sizeof(double) * (size_t)n * k;
   TK_TRY(Vb.alloc(nk, s));
@@ -526,8 +547,13 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     const double cc = 0.5 * b, e = std::max(0.5 * b, 1e-300);
     const int jw = std::min(J - nl, ka2) - 1;  // last wanted active column
     const double gmax = (tha[0] - cc) / e, gw = (tha[jw] - cc) / e;
+    // Degree: wanted columns may not outgrow the last wanted one by more than growth_cap, and
+    // no column may grow by more than abs_cap (unwanted columns are not rescaled, so their
+    // pollution by the largest active directions must stay far below 1/eps).
     int d = 1;
-    while (d < dmax && cheb(d + 1, gmax) / cheb(d + 1, gw) <= growth_cap) ++d;
+    while (d < dmax && cheb(d + 1, gmax) / cheb(d + 1, gw) <= growth_cap &&
+           cheb(d + 1, gmax) <= abs_cap)
+      ++d;
     double* Xa = V + nl;
     double* Y0 = T1.as<double>();
     double* Y1 = T2.as<double>();
@@ -544,20 +570,28 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
       TK_TRY(deflate(V, k, Y0, ka2, n, nl, ka2, P.as<double>(), s));
       double* t = Y0; Y0 = Y1; Y1 = t;
     }
-    std::vector<double> sc(ka2);
-    for (int i = 0; i < ka2; ++i) {
-      const double gi = (tha[i] - cc) / e;
-      sc[i] = gi >= 1.0 ? 1.0 / std::max(1.0, cheb(d, gi)) : 1.0;
-    }
-    TK_CUDA(cudaMemcpyAsync(rn.p, sc.data(), sizeof(double) * ka2, cudaMemcpyHostToDevice, s));
-    scale_cols<<<ceil_div((int64_t)n * ka2, 256), 256, 0, s>>>(Y1, ka2, n, ka2, rn.as<double>());
-    TK_LAUNCH();
     TK_TRY(copy_cols_f64(n, ka2, Y1, ka2, Xa, k, s));
     for (int rep = 0; rep < 2; ++rep) TK_TRY(deflate(V, k, Xa, k, n, nl, ka2, P.as<double>(), s));
-    TK_TRY(cholqr2(Xa, k, n, ka2, T3.as<double>(), Gk.as<double>(), R.as<double>(),
-                   Ri.as<double>(), stat.as<int>(), s));
+    normalize_cols_inplace<<<ka2, 256, 0, s>>>(Xa, k, n);
+    TK_LAUNCH();
+    const int qs = cholqr2(Xa, k, n, ka2, T3.as<double>(), Gk.as<double>(), R.as<double>(),
+                           Ri.as<double>(), stat.as<int>(), s);
+    if (qs != TUCKER_OK) {
+      char msg[256];
+      snprintf(msg, sizeof(msg),
+               "eigensolver: Cholesky-QR failed (n=%d J=%d k=%d outer=%d locked=%d degree=%d)",
+               n, J, k, outer, nl, d);
+      set_error_detail(msg);
+      return qs;
+    }
   }
-  if (!done) return TUCKER_ENOTCONV;
+  if (!done) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "eigensolver: %d outer iterations, %d of %d locked (n=%d)",
+             max_outer, nl, J, n);
+    set_error_detail(msg);
+    return TUCKER_ENOTCONV;
+  }
   sign_fix_out<<<J, 256, 0, s>>>(V, k, n, U, J);
   TK_LAUNCH();
   if (lambda)

@@ -1,5 +1,6 @@
 // Internal host-side interfaces between the translation units of the Tucker library.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -71,6 +72,25 @@ int syrk_f64(int rows, const double* Y1, int64_t K1, const double* Y2, int64_t K
 int copy_cols_f64(int rows, int cols, const double* src, int64_t lds, double* dst, int64_t ldd,
                   cudaStream_t s);
 int scale_f64(int64_t n, double alpha, double* x, cudaStream_t s);
+
+// mixed.cu (FP32 projections written as BF16 hi/lo pairs for the tensor-core Gram)
+int f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+int f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t s);
+int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int Jm,
+               const float* Uo, int Jo, __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY,
+               float* Y32, cudaStream_t s);
+int slice_proj_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int Jm,
+                     __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, cudaStream_t s);
+
+// gram_tc.cu: M = sum_t Y_t Y_t^T on tcgen05 with Y_t = hi + lo (BF16x3), FP64 result.
+struct GramTerm {
+  const __nv_bfloat16* hi;
+  const __nv_bfloat16* lo;
+  int64_t K;   // columns used
+  int64_t ld;  // row stride in elements, a multiple of 64; columns K..ld-1 are zero
+};
+int64_t gram_ld(int64_t K);
+int gram_bf16x3(int rows, int nterms, const GramTerm* terms, double* M, cudaStream_t s);
 
 // eig.cu
 struct EigStats {

@@ -1,0 +1,249 @@
+// Mixed-precision projections for the tensor-core Gram:
+//   ttmc_mixed        HOOI's Y = X x_m U_m^T x_o U_o^T (Figure hooi3) with FP32 factors and
+//                     FP32 accumulation;
+//   slice_proj_mixed  SP/MP's Y = X x_m U_m^T (Figures sp3, mp3), FP32.
+// Both write Y_(n) split into two BF16 matrices, Y = hi + lo (hi = bf16(y), lo = bf16(y - hi)),
+// row-major with rows padded to a multiple of 64 columns (zeros), the layout the BF16x3 Gram
+// reads with TMA.  HOOI's projection can also be written in FP32 for the core.
+// As in the FP64 kernels, every output element has one writer and a fixed summation order.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace tk {
+
+namespace {
+
+__device__ __forceinline__ void split_store(float y, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                            int64_t off) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(y);
+  hi[off] = h;
+  lo[off] = __float2bfloat16_rn(y - __bfloat162float(h));
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (float)a[t];
+}
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = (double)a[t];
+}
+
+template <int AP, int AQ>
+__global__ void __launch_bounds__(256)
+ttmc_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __restrict__ fiber_idx,
+                  const int64_t* __restrict__ fiber_ptr, const int32_t* __restrict__ leaf_idx,
+                  const float* __restrict__ val, const float* __restrict__ Um, int Jm,
+                  const float* __restrict__ Uo, int Jo, __nv_bfloat16* __restrict__ Yh,
+                  __nv_bfloat16* __restrict__ Yl, int64_t ldY, float* __restrict__ Y32) {
+  constexpr int TP = 16 * AP, TQ = 16 * AQ, FC = 64, RQ = (TQ + 31) / 32;
+  __shared__ float su[FC][TP];
+  __shared__ float st[FC][TQ];
+  const int i = blockIdx.x;
+  const int p0 = blockIdx.y * TP, q0 = blockIdx.z * TQ;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float acc[AP][AQ];
+#pragma unroll
+  for (int a = 0; a < AP; ++a)
+#pragma unroll
+    for (int b = 0; b < AQ; ++b) acc[a][b] = 0.f;
+  const int64_t fb = root_ptr[i], fe = root_ptr[i + 1];
+  for (int64_t fc = fb; fc < fe; fc += FC) {
+    const int nc = (int)min64(FC, fe - fc);
+    for (int c = warp; c < nc; c += 8) {
+      const int64_t f = fc + c;
+      const int64_t l0 = fiber_ptr[f], l1 = fiber_ptr[f + 1];
+      const int64_t im = fiber_idx[f];
+      for (int tp = lane; tp < TP; tp += 32)
+        su[c][tp] = (p0 + tp < Jm) ? Um[im * Jm + p0 + tp] : 0.f;
+      float t[RQ];
+#pragma unroll
+      for (int r = 0; r < RQ; ++r) t[r] = 0.f;
+      for (int64_t l = l0; l < l1; ++l) {
+        const float x = val[l];
+        const float* row = Uo + (int64_t)leaf_idx[l] * Jo + q0;
+#pragma unroll
+        for (int r = 0; r < RQ; ++r) {
+          const int q = lane + 32 * r;
+          if (q < TQ && q0 + q < Jo) t[r] = fmaf(x, row[q], t[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RQ; ++r) {
+        const int q = lane + 32 * r;
+        if (q < TQ) st[c][q] = t[r];
+      }
+    }
+    __syncthreads();
+    for (int c = 0; c < nc; ++c) {
+      float uu[AP], tt[AQ];
+#pragma unroll
+      for (int a = 0; a < AP; ++a) uu[a] = su[c][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < AQ; ++b) tt[b] = st[c][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < AP; ++a)
+#pragma unroll
+        for (int b = 0; b < AQ; ++b) acc[a][b] = fmaf(uu[a], tt[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  const int64_t K = (int64_t)Jm * Jo;
+#pragma unroll
+  for (int a = 0; a < AP; ++a) {
+    const int p = p0 + ty + 16 * a;
+    if (p >= Jm) continue;
+#pragma unroll
+    for (int b = 0; b < AQ; ++b) {
+      const int q = q0 + tx + 16 * b;
+      if (q >= Jo) continue;
+      const int64_t col = (int64_t)p * Jo + q;
+      if (Yh) split_store(acc[a][b], Yh, Yl, (int64_t)i * ldY + col);
+      if (Y32) Y32[(int64_t)i * K + col] = acc[a][b];
+    }
+  }
+  if (Yh && blockIdx.y == 0 && blockIdx.z == 0) {
+    for (int64_t c = K + threadIdx.x; c < ldY; c += blockDim.x) {
+      Yh[(int64_t)i * ldY + c] = __float2bfloat16_rn(0.f);
+      Yl[(int64_t)i * ldY + c] = __float2bfloat16_rn(0.f);
+    }
+  }
+}
+
+// One CTA per root slice i_n of ordering (n, o, m); warps take the slice's fibers (i_n, i_o) in
+// turn.  Each warp also zero-fills the columns of the i_o values between its fiber and the
+// previous one, so every element of row i_n (including the padding) is written exactly once.
+template <int NP>
+__global__ void __launch_bounds__(256)
+slice_proj_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __restrict__ fiber_idx,
+                        const int64_t* __restrict__ fiber_ptr, const int32_t* __restrict__ leaf_idx,
+                        const float* __restrict__ val, const float* __restrict__ Um, int Jm,
+                        int64_t Io, __nv_bfloat16* __restrict__ Yh, __nv_bfloat16* __restrict__ Yl,
+                        int64_t ldY) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t i = blockIdx.x;
+  __nv_bfloat16* rh = Yh + i * ldY;
+  __nv_bfloat16* rl = Yl + i * ldY;
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  const int64_t fb = root_ptr[i], fe = root_ptr[i + 1];
+  if (fb == fe) {
+    for (int64_t c = threadIdx.x; c < ldY; c += blockDim.x) {
+      rh[c] = z;
+      rl[c] = z;
+    }
+    return;
+  }
+  for (int64_t f = fb + warp; f < fe; f += nw) {
+    const int64_t io = fiber_idx[f];
+    const int64_t gap0 = (f == fb) ? 0 : (int64_t)(fiber_idx[f - 1] + 1) * Jm;
+    for (int64_t c = gap0 + lane; c < io * Jm; c += 32) {
+      rh[c] = z;
+      rl[c] = z;
+    }
+    if (f == fe - 1) {
+      for (int64_t c = (io + 1) * Jm + lane; c < ldY; c += 32) {
+        rh[c] = z;
+        rl[c] = z;
+      }
+    }
+    const int64_t l0 = fiber_ptr[f], l1 = fiber_ptr[f + 1];
+    for (int pc = 0; pc < Jm; pc += 32 * NP) {
+      float acc[NP];
+#pragma unroll
+      for (int r = 0; r < NP; ++r) acc[r] = 0.f;
+      for (int64_t l = l0; l < l1; ++l) {
+        const float x = val[l];
+        const float* row = Um + (int64_t)leaf_idx[l] * Jm + pc;
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+          const int p = lane + 32 * r;
+          if (pc + p < Jm) acc[r] = fmaf(x, row[p], acc[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NP; ++r) {
+        const int p = lane + 32 * r;
+        if (pc + p < Jm) split_store(acc[r], rh, rl, io * Jm + pc + p);
+      }
+    }
+  }
+}
+
+template <int AP, int AQ>
+void launch_ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int Jm,
+                       const float* Uo, int Jo, __nv_bfloat16* Yh, __nv_bfloat16* Yl,
+                       int64_t ldY, float* Y32, cudaStream_t s) {
+  dim3 grid((unsigned)X->dims[o->n], ceil_div(Jm, 16 * AP), ceil_div(Jo, 16 * AQ));
+  ttmc_mixed_kernel<AP, AQ><<<grid, 256, 0, s>>>(o->root_ptr, o->fiber_idx, o->fiber_ptr,
+                                                 o->leaf_idx, o->val_f32, Um, Jm, Uo, Jo, Yh, Yl,
+                                                 ldY, Y32);
+}
+
+int tcode(int J) { return J <= 16 ? 1 : (J <= 32 ? 2 : 4); }
+
+}  // namespace
+
+int f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+  if (n <= 0) return TUCKER_OK;
+  f64_to_f32_kernel<<<ceil_div(n, 256), 256, 0, s>>>(a, b, n);
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+int f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t s) {
+  if (n <= 0) return TUCKER_OK;
+  f32_to_f64_kernel<<<ceil_div(n, 256), 256, 0, s>>>(a, b, n);
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+int ensure_val_f32(tucker_tensor_s* X, Ordering* ord, cudaStream_t s) {
+  if (ord->val_f32) return TUCKER_OK;
+  TK_CUDA(cudaMalloc(&ord->val_f32, sizeof(float) * (size_t)(X->nnz ? X->nnz : 1)));
+  return f64_to_f32(ord->val, ord->val_f32, X->nnz, s);
+}
+
+int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int Jm,
+               const float* Uo, int Jo, __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY,
+               float* Y32, cudaStream_t s) {
+  if (X->dims[o->n] == 0) return TUCKER_OK;
+  const double nnz = (double)X->nnz, F = (double)o->F;
+  ProfScope prof("ttmc_mixed", s, 2.0 * (nnz * Jo + F * Jm * Jo),
+                 8.0 * nnz + 12.0 * F + (Yh ? 4.0 : 0.0) * X->dims[o->n] * (double)Jm * Jo +
+                     (Y32 ? 4.0 : 0.0) * X->dims[o->n] * (double)Jm * Jo +
+                     4.0 * (X->dims[o->m] * (double)Jm + X->dims[o->o] * (double)Jo));
+  const int cp = tcode(Jm), cq = tcode(Jo);
+#define TK_TM(A, B) \
+  if (cp == A && cq == B) launch_ttmc_mixed<A, B>(X, o, Um, Jm, Uo, Jo, Yh, Yl, ldY, Y32, s);
+  TK_TM(1, 1) TK_TM(1, 2) TK_TM(1, 4) TK_TM(2, 1) TK_TM(2, 2) TK_TM(2, 4) TK_TM(4, 1)
+  TK_TM(4, 2) TK_TM(4, 4)
+#undef TK_TM
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+int slice_proj_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int Jm,
+                     __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, cudaStream_t s) {
+  // ordering (n, o, m): fibers (i_n, i_o), leaves i_m.
+  const int64_t In = X->dims[o->n], Io = X->dims[o->m];
+  if (In == 0) return TUCKER_OK;
+  ProfScope prof("slice_proj_mixed", s, 2.0 * (double)X->nnz * Jm,
+                 8.0 * X->nnz + 16.0 * o->F + 4.0 * (double)In * Io * Jm +
+                     4.0 * X->dims[o->o] * (double)Jm);
+  const int np = Jm <= 32 ? 1 : (Jm <= 64 ? 2 : (Jm <= 128 ? 4 : 8));
+#define TK_SPM(N)                                                                           \
+  if (np == N)                                                                              \
+    slice_proj_mixed_kernel<N><<<(unsigned)In, 256, 0, s>>>(o->root_ptr, o->fiber_idx,      \
+                                                            o->fiber_ptr, o->leaf_idx,      \
+                                                            o->val_f32, Um, Jm, Io, Yh, Yl, \
+                                                            ldY);
+  TK_SPM(1) TK_SPM(2) TK_SPM(4) TK_SPM(8)
+#undef TK_SPM
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+}  // namespace tk

@@ -195,6 +195,10 @@ __global__ void unfold_gram_f64_kernel(const int64_t* __restrict__ r_root_ptr,
 int ttmc_f64(const tucker_tensor_s* X, const Ordering* o, const double* Um, int Jm,
              const double* Uo, int Jo, double* Y, cudaStream_t s) {
   if (X->dims[o->n] == 0) return TUCKER_OK;
+  const double nnz = (double)X->nnz, F = (double)o->F;
+  ProfScope prof("ttmc_f64", s, 2.0 * (nnz * Jo + F * Jm * Jo),
+                 12.0 * nnz + 12.0 * F + 8.0 * X->dims[o->n] * (double)Jm * Jo +
+                     8.0 * (X->dims[o->m] * (double)Jm + X->dims[o->o] * (double)Jo));
   const int cp = tile_code(Jm), cq = tile_code(Jo);
 #define TK_TT(A, B) \
   if (cp == A && cq == B) launch_ttmc<A, B>(X, o, Um, Jm, Uo, Jo, Y, s);
@@ -209,6 +213,9 @@ int slice_proj_f64(const tucker_tensor_s* X, const Ordering* o, const double* Um
                    double* Y, cudaStream_t s) {
   // ordering (n, o, m): fibers are (i_n, i_o), leaves i_m.
   const int64_t In = X->dims[o->n], Io = X->dims[o->m];
+  ProfScope prof("slice_proj_f64", s, 2.0 * (double)X->nnz * Jm,
+                 12.0 * X->nnz + 16.0 * o->F + 8.0 * (double)In * Io * Jm +
+                     8.0 * X->dims[o->o] * (double)Jm);
   TK_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)(In * Io * Jm), s));
   if (o->F == 0) return TUCKER_OK;
   const int64_t wpb = 8;
@@ -241,6 +248,7 @@ int unfolding_gram_f64(const tucker_tensor_s* X, const Ordering* rows, const Ord
   Buf st;
   TK_TRY(st.alloc(sizeof(int), s));
   TK_CUDA(cudaMemsetAsync(st.p, 0, sizeof(int), s));
+  ProfScope prof("unfold_gram_f64", s, 0.0, 12.0 * 2 * X->nnz + 8.0 * In * In);
   unfold_gram_f64_kernel<<<In, nw * 32, smem, s>>>(
       rows->root_ptr, rows->fiber_idx, rows->fiber_ptr, rows->leaf_idx, rows->val,
       fib->fiber_map, Io, fib->fiber_ptr, fib->leaf_idx, fib->val, In, M, st.as<int>());

@@ -74,6 +74,16 @@ _SIGS = {
                                   c_void_p]),
     "tucker_core": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_void_p,
                               POINTER(c_double), c_void_p]),
+    "tucker_ttmc_mixed": (c_int32, [c_void_p, c_int32, c_void_p, c_int32, c_void_p, c_int32,
+                                    c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    "tucker_slice_proj_mixed": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_int32,
+                                          c_void_p, c_void_p, c_int64, c_void_p]),
+    "tucker_gram_bf16x3": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p,
+                                     c_int64, c_int64, c_int32, c_void_p, c_void_p]),
+    "tucker_profile_enable": (None, [c_int32]),
+    "tucker_profile_query": (c_int32, [c_char_p, POINTER(c_int64), POINTER(c_double),
+                                       POINTER(c_double), POINTER(c_double)]),
+    "tucker_launch_count": (c_int64, []),
 }
 
 
@@ -217,38 +227,46 @@ def _opts(precision, tol, max_iter, init):
     return o, keep
 
 
-def _run(fn_name, X: Tensor, J, precision, tol, max_iter, init):
+def _run(fn_name, X: Tensor, J, precision, tol, max_iter, init, out="device"):
+    """Calls one method; results land in device memory (out="device") or in pinned host
+    memory (out="host", the library copies them back itself)."""
     torch = _torch()
     o, keep = _opts(precision, tol, max_iter, init)
-    G = torch.empty(tuple(int(j) for j in J), dtype=torch.float64, device="cuda")
-    U = [torch.empty((X.dims[a], int(J[a])), dtype=torch.float64, device="cuda") for a in range(3)]
-    fh = torch.empty(max(1, int(max_iter)), dtype=torch.float64, device="cuda")
+    if out == "host":
+        alloc = lambda shape: torch.empty(shape, dtype=torch.float64).pin_memory()  # noqa: E731
+        where = TUCKER_HOST
+    else:
+        alloc = lambda shape: torch.empty(shape, dtype=torch.float64, device="cuda")  # noqa: E731
+        where = TUCKER_DEVICE
+    G = alloc(tuple(int(j) for j in J))
+    U = [alloc((X.dims[a], int(J[a]))) for a in range(3)]
+    fh = alloc((max(1, int(max_iter)),))
     r = tucker_result()
     r.G = G.data_ptr()
     for a in range(3):
         r.U[a] = U[a].data_ptr()
     r.fit_history = fh.data_ptr()
-    r.where = TUCKER_DEVICE
+    r.where = where
     _check(getattr(_lib(), fn_name)(X.handle, _J(J), ctypes.byref(o), ctypes.byref(r)), fn_name)
     iters = int(r.iters)
     return dict(G=G, U=U, fit=float(r.fit), iters=iters,
                 fit_history=fh[:iters].cpu().numpy().tolist(), rank_deficient=int(r.rank_deficient))
 
 
-def tucker_hosvd(X: Tensor, J, precision="fp64"):
-    return _run("tucker_hosvd", X, J, precision, 0.0, 1, None)
+def tucker_hosvd(X: Tensor, J, precision="fp64", out="device"):
+    return _run("tucker_hosvd", X, J, precision, 0.0, 1, None, out)
 
 
-def tucker_hooi(X: Tensor, J, tol=1e-4, max_iter=50, precision="fp64", init=None):
-    return _run("tucker_hooi", X, J, precision, tol, max_iter, init)
+def tucker_hooi(X: Tensor, J, tol=1e-4, max_iter=50, precision="fp64", init=None, out="device"):
+    return _run("tucker_hooi", X, J, precision, tol, max_iter, init, out)
 
 
-def tucker_sp(X: Tensor, J, C_raw, tol=1e-4, max_iter=50, precision="fp64"):
-    return _run("tucker_sp", X, J, precision, tol, max_iter, [None, None, C_raw])
+def tucker_sp(X: Tensor, J, C_raw, tol=1e-4, max_iter=50, precision="fp64", out="device"):
+    return _run("tucker_sp", X, J, precision, tol, max_iter, [None, None, C_raw], out)
 
 
-def tucker_mp(X: Tensor, J, tol=1e-4, max_iter=50, precision="fp64"):
-    return _run("tucker_mp", X, J, precision, tol, max_iter, None)
+def tucker_mp(X: Tensor, J, tol=1e-4, max_iter=50, precision="fp64", out="device"):
+    return _run("tucker_mp", X, J, precision, tol, max_iter, None, out)
 
 
 # ---- step entry points -------------------------------------------------------------------------
@@ -341,6 +359,85 @@ def tucker_core(X: Tensor, A, B, C):
     _check(_lib().tucker_core(X.handle, _dptr(A), _dptr(B), _dptr(C), _J(J), _dptr(G),
                               ctypes.byref(g2), _stream()), "tucker_core")
     return G, float(g2.value)
+
+
+def gram_ld(K: int) -> int:
+    """Row stride (elements) of a split BF16 matrix with K columns: K rounded up to 64."""
+    return (int(K) + 63) // 64 * 64
+
+
+def _split_buffers(rows, K):
+    torch = _torch()
+    ld = gram_ld(K)
+    hi = torch.empty((rows, ld), dtype=torch.bfloat16, device="cuda")
+    lo = torch.empty((rows, ld), dtype=torch.bfloat16, device="cuda")
+    return hi, lo, ld
+
+
+def _dev_f32(a):
+    torch = _torch()
+    if isinstance(a, np.ndarray):
+        a = torch.from_numpy(np.ascontiguousarray(a))
+    return a.to(device="cuda", dtype=torch.float32).contiguous()
+
+
+def tucker_ttmc_mixed(X: Tensor, n, Um, Uo, split=True, fp32=False):
+    """Returns (hi, lo, Y32): the split BF16 Y_(n) (rows padded to 64 columns) and/or FP32 Y_(n)."""
+    torch = _torch()
+    Um, Uo = _dev_f32(Um), _dev_f32(Uo)
+    K = Um.shape[1] * Uo.shape[1]
+    hi = lo = Y32 = None
+    ld = 0
+    if split:
+        hi, lo, ld = _split_buffers(X.dims[n], K)
+    if fp32:
+        Y32 = torch.empty((X.dims[n], K), dtype=torch.float32, device="cuda")
+    _check(_lib().tucker_ttmc_mixed(X.handle, n, _dptr(Um), Um.shape[1], _dptr(Uo), Uo.shape[1],
+                                    _dptr(hi) if split else None, _dptr(lo) if split else None,
+                                    ld, _dptr(Y32) if fp32 else None, _stream()),
+           "tucker_ttmc_mixed")
+    return hi, lo, Y32
+
+
+def tucker_slice_proj_mixed(X: Tensor, n, m, Um):
+    o = 3 - n - m
+    Um = _dev_f32(Um)
+    hi, lo, ld = _split_buffers(X.dims[n], X.dims[o] * Um.shape[1])
+    _check(_lib().tucker_slice_proj_mixed(X.handle, n, m, _dptr(Um), Um.shape[1], _dptr(hi),
+                                          _dptr(lo), ld, _stream()), "tucker_slice_proj_mixed")
+    return hi, lo
+
+
+def tucker_gram_bf16x3(Y1, Y2=None, K1=None, K2=None):
+    """Y1, Y2: (hi, lo) pairs of BF16 CUDA tensors [rows, ld]; K: used columns (default ld)."""
+    torch = _torch()
+    h1, l1 = Y1
+    rows, ld1 = h1.shape
+    M = torch.empty((rows, rows), dtype=torch.float64, device="cuda")
+    args = [_dptr(h1), _dptr(l1), int(K1 if K1 is not None else ld1), ld1]
+    if Y2 is not None:
+        h2, l2 = Y2
+        args += [_dptr(h2), _dptr(l2), int(K2 if K2 is not None else h2.shape[1]), h2.shape[1]]
+    else:
+        args += [None, None, 0, 0]
+    _check(_lib().tucker_gram_bf16x3(*args, rows, _dptr(M), _stream()), "tucker_gram_bf16x3")
+    return M
+
+
+def tucker_profile_enable(on: bool):
+    _lib().tucker_profile_enable(1 if on else 0)
+
+
+def tucker_profile_query(name: str):
+    """(launches, total_ms, algorithmic_flops, algorithmic_bytes) recorded for kernel `name`."""
+    n, ms, f, b = c_int64(), c_double(), c_double(), c_double()
+    _check(_lib().tucker_profile_query(name.encode(), ctypes.byref(n), ctypes.byref(ms),
+                                       ctypes.byref(f), ctypes.byref(b)), "tucker_profile_query")
+    return int(n.value), float(ms.value), float(f.value), float(b.value)
+
+
+def tucker_launch_count() -> int:
+    return int(_lib().tucker_launch_count())
 
 
 def header_functions(header_path=None):
