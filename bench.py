@@ -132,42 +132,101 @@ def make_inputs(rank):
     return X, C_raw
 
 
-def run_job(tk, make_tensor, C_raw, out):
+def run_job(tk, make_tensor, C_raw, out, precision="fp64"):
     """One step: CSF build + HO-SVD + HOOI/SP/MP x SWEEPS.  Returns (fits, sweeps)."""
     T = make_tensor()
     fits = {}
-    fits["hosvd"] = tk.tucker_hosvd(T, CORE, out=out)["fit"]
-    fits["hooi"] = tk.tucker_hooi(T, CORE, tol=-np.inf, max_iter=SWEEPS, out=out)["fit"]
-    fits["sp"] = tk.tucker_sp(T, CORE, C_raw, tol=-np.inf, max_iter=SWEEPS, out=out)["fit"]
-    fits["mp"] = tk.tucker_mp(T, CORE, tol=-np.inf, max_iter=SWEEPS, out=out)["fit"]
+    pr = precision
+    fits["hosvd"] = tk.tucker_hosvd(T, CORE, precision=pr, out=out)["fit"]
+    fits["hooi"] = tk.tucker_hooi(T, CORE, tol=-np.inf, max_iter=SWEEPS, precision=pr,
+                                  out=out)["fit"]
+    fits["sp"] = tk.tucker_sp(T, CORE, C_raw, tol=-np.inf, max_iter=SWEEPS, precision=pr,
+                              out=out)["fit"]
+    fits["mp"] = tk.tucker_mp(T, CORE, tol=-np.inf, max_iter=SWEEPS, precision=pr,
+                              out=out)["fit"]
     T.close()
     return fits, 1 + 3 * SWEEPS
 
 
-def cpu_sample(X, C_raw, repeats=1):
-    """The oracle on a bounded sample of the workload: HO-SVD plus one pass each of HOOI
-    (from HO-SVD's B, C), SP and MP.  Returns (seconds, passes)."""
+def timed_region(tk, torch, world, local, steps, make_tensor, C_raw, l2buf, precision):
+    """Device-timed steps with profiling on.  Returns (total_ms, passes, fits, launches,
+    clocks, per-kernel profile)."""
+    clocks = ClockSampler(local)
+    tk.tucker_profile_enable(True)
+    launches0 = tk.tucker_launch_count()
+    stream = torch.cuda.current_stream()
+    total_ms, passes, fits = 0.0, 0, None
+    barrier(world)
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush_l2(l2buf)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fits, p = run_job(tk, make_tensor, C_raw, "device", precision)
+        b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+        passes += p
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = tk.tucker_launch_count() - launches0
+    clk = clocks.stop()
+    prof = {}
+    for name in KERNELS:
+        n, ms, fl, by = tk.tucker_profile_query(name)
+        if n:
+            prof[name] = {"launches": n, "ms": ms, "flops": fl, "bytes": by}
+    tk.tucker_profile_enable(False)
+    return total_ms, passes, fits, launches, clk, prof
+
+
+KERNELS = ("syrk_f64", "gram_bf16x3", "ttmc_f64", "ttmc_mixed", "slice_proj_f64",
+           "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64", "gemm_nn_f32", "jacobi_f64",
+           "csf_build")
+
+
+def roofline_of(prof, name, total_ms, bound, peak, unit, peak_source, per="flops"):
+    d = prof.get(name)
+    if not d:
+        return None
+    per_launch_ms = d["ms"] / d["launches"]
+    work = (d["flops"] if per == "flops" else d["bytes"]) / d["launches"]
+    scale = 1e12 if unit == "TFLOP/s" else 1e9
+    achieved = work / (per_launch_ms * 1e-3) / scale if per_launch_ms else 0.0
+    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_source,
+            "share_of_step": d["ms"] / total_ms, "launches": d["launches"]}
+
+
+CPU_SAMPLE = "one HOOI pass (3 projections, Grams, eigensolves, core, fit) from the HO-SVD B, C"
+
+
+def cpu_setup(X):
+    """Untimed: the HO-SVD start of HOOI that the CPU sample continues from."""
+    from oracle import tucker_oracle as O
+    return [None] + [O.leading_eigvecs(O.unfolding_gram(X.dims, X.idx, X.val, n), CORE[n])[0]
+                     for n in (1, 2)]
+
+
+def cpu_sample(X, init):
+    """The oracle on a bounded sample of the workload (one HOOI pass).  Returns (s, passes)."""
     from oracle import tucker_oracle as O
     t0 = time.perf_counter()
-    passes = 0
-    for _ in range(repeats):
-        h = O.hosvd(X.dims, X.idx, X.val, CORE)
-        O.hooi(X.dims, X.idx, X.val, CORE, -np.inf, 1, init=[None, h["U"][1], h["U"][2]])
-        O.sp(X.dims, X.idx, X.val, CORE, C_raw, -np.inf, 1)
-        O.mp(X.dims, X.idx, X.val, CORE, -np.inf, 1)
-        passes += 4
-    return time.perf_counter() - t0, passes
+    O.hooi(X.dims, X.idx, X.val, CORE, -np.inf, 1, init=init)
+    return time.perf_counter() - t0, 1
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    X, C_raw = make_inputs(0)
+    X, _ = make_inputs(0)
+    init = cpu_setup(X)
     for _ in range(args.warmup):
-        cpu_sample(X, C_raw)
+        cpu_sample(X, init)
     tot, passes = 0.0, 0
     for _ in range(args.steps):
-        dt, p = cpu_sample(X, C_raw)
+        dt, p = cpu_sample(X, init)
         tot += dt
         passes += p
     value = passes / tot
@@ -175,10 +234,9 @@ def run_reference(args, world, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "per step: HO-SVD + 1 pass each of HOOI, "
-                       "SP, MP (4 passes)"},
+            "config": {"workload": WORKLOAD, "sample": "per step: " + CPU_SAMPLE},
             "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": os.cpu_count(),
-                             "kind": "oracle", "sample": "HO-SVD + 1 pass each of HOOI, SP, MP"},
+                             "kind": "oracle", "sample": CPU_SAMPLE},
             "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -221,37 +279,18 @@ def main():
         run_job(tk, dev_tensor, C_raw, "device")
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region -----------------------------------------------------
-    clocks = ClockSampler(local)
-    tk.tucker_profile_enable(True)
-    launches0 = tk.tucker_launch_count()
-    stream = torch.cuda.current_stream()
-    total_ms, passes, fits = 0.0, 0, None
-    barrier(world)
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush_l2(l2buf)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        fits, p = run_job(tk, dev_tensor, C_raw, "device")
-        b.record(stream)
-        b.synchronize()
-        total_ms += a.elapsed_time(b)
-        passes += p
-    torch.cuda.synchronize()
-    barrier(world)
-    launches = tk.tucker_launch_count() - launches0
-    clk = clocks.stop()
-    prof = {}
-    for name in ("syrk_f64", "ttmc_f64", "slice_proj_f64", "unfold_gram_f64", "gemm_nn_f64",
-                 "jacobi_f64", "csf_build"):
-        n, ms, fl, by = tk.tucker_profile_query(name)
-        prof[name] = {"launches": n, "ms": ms, "flops": fl, "bytes": by}
-    tk.tucker_profile_enable(False)
-
+    # ---- device-resident timed region (FP64: the workload as configured) --------------------
+    total_ms, passes, fits, launches, clk, prof = timed_region(
+        tk, torch, world, local, args.steps, dev_tensor, C_raw, l2buf, "fp64")
     t_max = max_over_ranks(total_ms, world)
     value = passes * world / (t_max / 1e3)
+
+    # ---- the same workload in the mixed-precision form -------------------------------------
+    for _ in range(min(args.warmup, 1)):
+        run_job(tk, dev_tensor, C_raw, "device", "mixed")
+    mx_ms, mx_passes, mx_fits, mx_launches, mx_clk, mx_prof = timed_region(
+        tk, torch, world, local, args.steps, dev_tensor, C_raw, l2buf, "mixed")
+    mx_value = mx_passes * world / (max_over_ranks(mx_ms, world) / 1e3)
 
     # ---- end to end through the C ABI with host buffers -------------------------------------
     e2e_ms, e2e_passes = 0.0, 0
@@ -272,26 +311,26 @@ def main():
     if rank != 0:
         return
 
-    # ---- roofline of the dominant kernel ----------------------------------------------------
+    # ---- rooflines ---------------------------------------------------------------------------
+    fp64_src = "nominal GB300 FP64 rate 1.25 TFLOP/s (no measured FP64 figure)"
     dom = max(prof, key=lambda k: prof[k]["ms"])
-    d = prof[dom]
-    per_launch_ms = d["ms"] / max(d["launches"], 1)
-    flops_per_launch = d["flops"] / max(d["launches"], 1)
-    achieved_tflops = flops_per_launch / (per_launch_ms * 1e-3) / 1e12 if per_launch_ms else 0.0
-    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved_tflops,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal GB300 FP64 rate (no measured FP64 figure)",
-                "share_of_step": d["ms"] / total_ms}
-    tt = prof["ttmc_f64"]
-    ttmc_gbs = tt["bytes"] / (tt["ms"] * 1e-3) / 1e9 if tt["ms"] else None
+    roofline = roofline_of(prof, dom, total_ms, "alu", FP64_PEAK_TFLOPS, "TFLOP/s", fp64_src)
+    tt = prof.get("ttmc_f64")
+    ttmc_gbs = tt["bytes"] / (tt["ms"] * 1e-3) / 1e9 if tt and tt["ms"] else None
+    bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+    mx_gram = roofline_of(mx_prof, "gram_bf16x3", mx_ms, "tensor", bf16, "TFLOP/s",
+                          f"{peak_src} bf16 sustained (cuBLAS), algorithmic FP32-equivalent "
+                          "Gram FLOPs (the BF16x3 kernel issues 3x as many)")
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        secs, p = cpu_sample(X, C_raw)
+        secs, p = cpu_sample(X, cpu_setup(X))
         cpu = {"value": p / secs, "unit": "sweeps/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "HO-SVD + 1 pass each of HOOI (from HO-SVD B, C), SP, MP on the same "
-                         f"tensor: {p} passes in {secs:.1f} s"}
+               "sample": f"{CPU_SAMPLE}, same tensor: {p} pass in {secs:.1f} s"}
+
+    def kern_table(pr, tot):
+        return {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                    "share": round(v["ms"] / tot, 4)} for k, v in pr.items()}
 
     line = {
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,
@@ -302,17 +341,22 @@ def main():
                    "l2": "flushed between steps (256 MB write); tensor 200 MB > L2",
                    "parallelism": f"replicas x{world}"},
         "fits": fits,
-        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                        "share": round(v["ms"] / total_ms, 4)} for k, v in prof.items()},
+        "kernels": kern_table(prof, total_ms),
         "ttmc_f64_gbs": ttmc_gbs,
         "roofline": roofline,
+        "mixed": {"value": mx_value, "unit": "sweeps/s", "ms_per_step": mx_ms / args.steps,
+                  "speedup_vs_fp64": mx_value / value,
+                  "max_abs_dfit_vs_fp64": max(abs(mx_fits[k] - fits[k]) for k in fits),
+                  "fits": mx_fits, "kernels": kern_table(mx_prof, mx_ms),
+                  "roofline_gram": mx_gram, "gpu_launches": mx_launches, "clocks": mx_clk},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
         "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs"),
-                  "bf16_tflops": peaks.get("bf16_tflops")},
+                  "bf16_tflops": peaks.get("bf16_tflops"),
+                  "bf16_tflops_sustained": peaks.get("bf16_tflops_sustained")},
     }
     print(json.dumps(line), flush=True)
 

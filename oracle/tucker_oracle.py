@@ -319,8 +319,10 @@ def mp_init_matrix(dims, idx, val, n):
     M = np.zeros((dims[n], dims[n]))
     for s in (m, o):                       # slice on mode s; the remaining free mode is r
         r = o if s == m else m
+        order = np.argsort(idx[s], kind="stable")          # group the nonzeros by slice
+        bounds = np.searchsorted(idx[s][order], np.arange(dims[s] + 1))
         for t in range(dims[s]):           # slice X_t: rows i_n, columns i_r, at i_s = t
-            sel = idx[s] == t
+            sel = order[bounds[t]:bounds[t + 1]]
             Xt = sps.csr_matrix((val[sel], (idx[n][sel], idx[r][sel])), shape=(dims[n], dims[r]))
             M += np.asarray((Xt @ Xt.T).todense())
     return M

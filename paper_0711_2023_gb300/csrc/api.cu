@@ -138,7 +138,7 @@ struct Run {
   Buf U[3], U32[3];
   Buf Y, Y2;                  // FP64 projections; Y also stages the core input
   Buf Yh, Yl, Y2h, Y2l, Y32;  // mixed projections
-  Buf M, G, sc;               // sc: [0] |G|^2, [1] fit
+  Buf M, M32, G, sc;          // sc: [0] |G|^2, [1] fit; M32: FP32 copy for the eigensolver
   int rank_def = 0;
   std::vector<double> fits;
   int64_t dim(int a) const { return X->dims[a]; }
@@ -154,6 +154,7 @@ int alloc_buffers(Run& r) {
   }
   const int64_t maxI = std::max(r.dim(0), std::max(r.dim(1), r.dim(2)));
   TK_TRY(r.M.alloc(sizeof(double) * maxI * maxI, r.s));
+  if (r.mixed) TK_TRY(r.M32.alloc(sizeof(float) * maxI * maxI, r.s));
   TK_TRY(r.G.alloc(sizeof(double) * J[0] * J[1] * J[2], r.s));
   TK_TRY(r.sc.alloc(sizeof(double) * 2, r.s));
   const size_t core_in = (size_t)(r.dim(2) * J[0] * J[1]);  // W_(3): I3 x J1 J2
@@ -178,13 +179,14 @@ int alloc_buffers(Run& r) {
   if (r.mixed) {
     TK_TRY(r.Y.alloc(core_in * sizeof(double), r.s));
     TK_TRY(r.Y32.alloc(core_in * sizeof(float), r.s));
+    // yb, yb2: bytes of one BF16 matrix (hi or lo) of the largest projection
     if (yb) {
-      TK_TRY(r.Yh.alloc(yb / 2, r.s));
-      TK_TRY(r.Yl.alloc(yb / 2, r.s));
+      TK_TRY(r.Yh.alloc(yb, r.s));
+      TK_TRY(r.Yl.alloc(yb, r.s));
     }
     if (yb2) {
-      TK_TRY(r.Y2h.alloc(yb2 / 2, r.s));
-      TK_TRY(r.Y2l.alloc(yb2 / 2, r.s));
+      TK_TRY(r.Y2h.alloc(yb2, r.s));
+      TK_TRY(r.Y2l.alloc(yb2, r.s));
     }
   } else {
     TK_TRY(r.Y.alloc(y, r.s));
@@ -200,8 +202,14 @@ int refresh32(Run& r, int n) {
 
 int eig_update(Run& r, int n, bool warm) {
   EigStats st;
+  const float* m32 = nullptr;
+  if (r.mixed) {
+    TK_TRY(f64_to_f32(r.M.as<double>(), r.M32.as<float>(), r.dim(n) * r.dim(n), r.s));
+    m32 = r.M32.as<float>();
+  }
   TK_TRY(eig_topk_f64(r.M.as<double>(), (int)r.dim(n), r.J[n], warm ? r.U[n].as<double>() : nullptr,
-                      r.U[n].as<double>(), nullptr, r.s, &st));
+                      r.U[n].as<double>(), nullptr, r.s, &st, m32,
+                      r.mixed ? EIG_TOL_MIXED : EIG_TOL_FP64));
   if (st.rank_deficient) r.rank_def |= 1 << n;
   return refresh32(r, n);
 }

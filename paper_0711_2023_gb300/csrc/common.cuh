@@ -115,36 +115,33 @@ __device__ __forceinline__ float warp_sumf(float v) {
   return v;
 }
 
-// Grid-wide barrier for cooperative launches, with a bounded spin.  `bar[0]` counts arrivals,
-// `bar[1]` is the generation.  Returns false (and sets DEV_TIMEOUT in *status) when the spin
-// limit runs out; callers then leave their loops.  All blocks of a cooperative launch are
-// co-resident, so in a healthy run every wait ends.
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* status) {
+// Grid-wide barrier for cooperative launches, with a bounded spin.  `*count` (zeroed before the
+// launch) only grows: barrier number e (1, 2, ...) completes when it reaches e * nblocks, so
+// each block makes one atomic per barrier and polls.  `*epoch` is the block's barrier count.
+// Returns false (and sets DEV_TIMEOUT in *status) when the spin limit runs out; callers then
+// leave their loops.  All blocks of a cooperative launch are co-resident, so in a healthy run
+// every wait ends.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int nblocks,
+                                             unsigned int* epoch, int* status) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok_s = 1;
-    volatile unsigned int* vgen = bar + 1;
-    unsigned int gen = *vgen;
+    const unsigned int target = (*epoch + 1) * nblocks;
     __threadfence();
-    unsigned int arrived = atomicAdd(bar, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == gen) {
-        if (++spins > (1ll << 24)) {  // about a second: far beyond any healthy wait
-          atomicOr(status, DEV_TIMEOUT);
-          ok_s = 0;
-          break;
-        }
-        __nanosleep(32);
+    atomicAdd(count, 1u);
+    volatile unsigned int* vc = count;
+    const long long t0 = clock64();
+    while (*vc < target) {
+      if (clock64() - t0 > 2000000000ll) {  // about a second: far beyond any healthy wait
+        atomicOr(status, DEV_TIMEOUT);
+        ok_s = 0;
+        break;
       }
     }
     __threadfence();
   }
+  ++*epoch;
   __syncthreads();
   return ok_s != 0;
 }

@@ -3,6 +3,8 @@
 // the core.  All reductions have a fixed order (split-K partials are summed in split order),
 // so results are bitwise reproducible.  FP64 arithmetic on this part is ALU-bound; the tiles
 // are sized for register reuse, not for bandwidth.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace tk {
@@ -11,32 +13,38 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
-// C = alpha * A B + beta * X + gamma * Z, 64 x 64 tile per CTA, 4 x 4 per thread.
+// C = alpha * A B + beta * X + gamma * Z, 64 x 64 tile per CTA, 4 x 4 per thread, products
+// and sums in TC (A stored as TA, B converted to TC on load; epilogue in FP64).  With P given,
+// the CTA instead writes its raw partial product over K-slice blockIdx.z (of length kchunk) to
+// P[blockIdx.z] and the epilogue is applied by reduce_nn.
+template <typename TA, typename TC>
 __global__ void __launch_bounds__(256)
-gemm_nn_kernel(int m, int n, int k, double alpha, const double* __restrict__ A, int64_t lda,
+gemm_nn_kernel(int m, int n, int k, double alpha, const TA* __restrict__ A, int64_t lda,
                const double* __restrict__ B, int64_t ldb, double beta, const double* Xm,
                int64_t ldx, double gamma, const double* __restrict__ Zm, int64_t ldz, double* C,
-               int64_t ldc) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN];
+               int64_t ldc, int kchunk, double* __restrict__ P) {
+  __shared__ TC As[BK][BM + 1];
+  __shared__ TC Bs[BK][BN];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  double acc[4][4] = {};
-  for (int k0 = 0; k0 < k; k0 += BK) {
+  TC acc[4][4] = {};
+  const int kb = blockIdx.z * kchunk;
+  const int ke = min(k, kb + kchunk);
+  for (int k0 = kb; k0 < ke; k0 += BK) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int idx = threadIdx.x + 256 * e;  // 0..1023
       const int ar = idx / BK, ac = idx % BK;  // A tile: 64 rows x 16 cols
       const int gr = m0 + ar, gc = k0 + ac;
-      As[ac][ar] = (gr < m && gc < k) ? A[(int64_t)gr * lda + gc] : 0.0;
+      As[ac][ar] = (gr < m && gc < ke) ? (TC)A[(int64_t)gr * lda + gc] : TC(0);
       const int br = idx / BN, bc = idx % BN;  // B tile: 16 rows x 64 cols
       const int hr = k0 + br, hc = n0 + bc;
-      Bs[br][bc] = (hr < k && hc < n) ? B[(int64_t)hr * ldb + hc] : 0.0;
+      Bs[br][bc] = (hr < ke && hc < n) ? (TC)B[(int64_t)hr * ldb + hc] : TC(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      TC a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -48,6 +56,20 @@ gemm_nn_kernel(int m, int n, int k, double alpha, const double* __restrict__ A, 
     }
     __syncthreads();
   }
+  if (P) {
+    double* Pz = P + (int64_t)blockIdx.z * m * n;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = m0 + ty + 16 * i;
+      if (r >= m) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = n0 + tx + 16 * j;
+        if (c < n) Pz[(int64_t)r * n + c] = acc[i][j];
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = m0 + ty + 16 * i;
@@ -56,7 +78,7 @@ gemm_nn_kernel(int m, int n, int k, double alpha, const double* __restrict__ A, 
     for (int j = 0; j < 4; ++j) {
       const int c = n0 + tx + 16 * j;
       if (c >= n) continue;
-      double v = alpha * acc[i][j];
+      double v = alpha * (double)acc[i][j];
       if (Xm) v = fma(beta, Xm[(int64_t)r * ldx + c], v);
       if (Zm) v = fma(gamma, Zm[(int64_t)r * ldz + c], v);
       C[(int64_t)r * ldc + c] = v;
@@ -110,6 +132,21 @@ gemm_tn_kernel(int m, int n, int64_t k, int64_t kchunk, const double* __restrict
       if (c < n) Pz[(int64_t)r * n + c] = acc[i][j];
     }
   }
+}
+
+// C = alpha * (sum of the split partials, in split order) + beta * X + gamma * Z.
+__global__ void reduce_nn(const double* __restrict__ P, int splits, int m, int n, double alpha,
+                          double beta, const double* Xm, int64_t ldx, double gamma,
+                          const double* __restrict__ Zm, int64_t ldz, double* C, int64_t ldc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * n) return;
+  const int64_t r = t / n, c = t % n;
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += P[(int64_t)z * m * n + t];
+  double v = alpha * s;
+  if (Xm) v = fma(beta, Xm[r * ldx + c], v);
+  if (Zm) v = fma(gamma, Zm[r * ldz + c], v);
+  C[r * ldc + c] = v;
 }
 
 __global__ void reduce_splits(const double* __restrict__ P, int splits, int m, int n,
@@ -222,17 +259,60 @@ int choose_splits(int tiles, int64_t k) {
 
 }  // namespace
 
+namespace {
+
+template <typename TA, typename TC>
+int gemm_nn_impl(const char* name, int m, int n, int k, double alpha, const TA* A, int64_t lda,
+                 const double* B, int64_t ldb, double beta, const double* Xm, int64_t ldx,
+                 double gamma, const double* Zm, int64_t ldz, double* C, int64_t ldc,
+                 cudaStream_t s) {
+  if (m <= 0 || n <= 0) return TUCKER_OK;
+  ProfScope prof(name, s, 2.0 * m * n * (double)k,
+                 (double)sizeof(TA) * m * k + 8.0 * ((double)k * n + (double)m * n));
+  const int tiles = ceil_div(n, BN) * ceil_div(m, BM);
+  // Skinny products (the eigensolver's M V with few columns) get too few tiles to fill the
+  // GPU: split K into slices summed in a fixed order by reduce_nn.
+  int splits = 1;
+  if (tiles < num_sms() && k >= 4 * BK) {
+    splits = std::min((2 * num_sms() + tiles - 1) / tiles, k / (2 * BK));
+    if (splits < 1) splits = 1;
+  }
+  if (splits == 1) {
+    dim3 grid(ceil_div(n, BN), ceil_div(m, BM), 1);
+    gemm_nn_kernel<TA, TC><<<grid, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, Xm, ldx,
+                                                gamma, Zm, ldz, C, ldc, k, nullptr);
+    TK_LAUNCH();
+    return TUCKER_OK;
+  }
+  int kchunk = (k + splits - 1) / splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  splits = (k + kchunk - 1) / kchunk;
+  Buf P;
+  TK_TRY(P.alloc(sizeof(double) * (size_t)splits * m * n, s));
+  dim3 grid(ceil_div(n, BN), ceil_div(m, BM), splits);
+  gemm_nn_kernel<TA, TC><<<grid, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, Xm, ldx, gamma,
+                                              Zm, ldz, C, ldc, kchunk, P.as<double>());
+  TK_LAUNCH();
+  reduce_nn<<<ceil_div((int64_t)m * n, 256), 256, 0, s>>>(P.as<double>(), splits, m, n, alpha,
+                                                          beta, Xm, ldx, gamma, Zm, ldz, C, ldc);
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+}  // namespace
+
 int gemm_nn_f64(int m, int n, int k, double alpha, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double beta, const double* Xm, int64_t ldx, double gamma,
                 const double* Zm, int64_t ldz, double* C, int64_t ldc, cudaStream_t s) {
-  if (m <= 0 || n <= 0) return TUCKER_OK;
-  ProfScope prof("gemm_nn_f64", s, 2.0 * m * n * (double)k,
-                 8.0 * ((double)m * k + (double)k * n + (double)m * n));
-  dim3 grid(ceil_div(n, BN), ceil_div(m, BM));
-  gemm_nn_kernel<<<grid, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, Xm, ldx, gamma, Zm,
-                                      ldz, C, ldc);
-  TK_LAUNCH();
-  return TUCKER_OK;
+  return gemm_nn_impl<double, double>("gemm_nn_f64", m, n, k, alpha, A, lda, B, ldb, beta, Xm,
+                                      ldx, gamma, Zm, ldz, C, ldc, s);
+}
+
+int gemm_nn_f32a(int m, int n, int k, double alpha, const float* A, int64_t lda, const double* B,
+                 int64_t ldb, double beta, const double* Xm, int64_t ldx, double gamma,
+                 const double* Zm, int64_t ldz, double* C, int64_t ldc, cudaStream_t s) {
+  return gemm_nn_impl<float, float>("gemm_nn_f32", m, n, k, alpha, A, lda, B, ldb, beta, Xm, ldx,
+                                    gamma, Zm, ldz, C, ldc, s);
 }
 
 int gemm_tn_f64(int m, int n, int64_t k, const double* A, int64_t lda, const double* B,

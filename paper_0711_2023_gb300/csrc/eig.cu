@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
   __syncthreads();
   const double abs_tol = 1e-17 * normA_s + 1e-300;
   const int64_t ntri = (int64_t)h * (h + 1) / 2;
+  unsigned int epoch = 0;
   int sweep = 0;
   bool alive = true;
   for (; sweep < g.max_sweeps && alive; ++sweep) {
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
         Qr[pi[I]] = c * qp - s * qq;
         Qr[qi[I]] = s * qp + c * qq;
       }
-      alive = grid_barrier(g.bar, gridDim.x, g.status);
+      alive = grid_barrier(g.bar, gridDim.x, &epoch, g.status);
       double* tmp = Acur; Acur = Anext; Anext = tmp;
     }
     if (!alive) break;
@@ -448,7 +449,7 @@ int deflate(const double* L, int64_t ldl, double* Va, int64_t ldv, int n, int nl
 }  // namespace
 
 int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, double* lambda,
-                 cudaStream_t s, EigStats* st) {
+                 cudaStream_t s, EigStats* st, const float* M32, double tol) {
   EigStats local;
   if (!st) st = &local;
   *st = EigStats();
@@ -472,7 +473,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     return TUCKER_OK;
   }
 
-  const double tol = 3e-13;
+  bool use32 = M32 != nullptr;
   const int max_outer = 120, dmax = 24;
   const double growth_cap = 1e4, abs_cap = 1e8;
   Buf Vb, T1, T2, T3, H, Qh, evh, Gk, R, Ri, P, rn, stat;
@@ -543,7 +544,9 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     // Chebyshev filter on the remaining active columns.
     const int ka2 = k - nl;
     const double* tha = th.data() + nlock;
-    const double b = tha[ka2 - 1];
+    // Unwanted interval [0, b]; when M has fewer than k nonzero eigenvalues the smallest Ritz
+    // value is ~0, so b is floored to keep the map (x - c) / e finite.
+    const double b = std::max(tha[ka2 - 1], 1e-10 * theta1);
     const double cc = 0.5 * b, e = std::max(0.5 * b, 1e-300);
     const int jw = std::min(J - nl, ka2) - 1;  // last wanted active column
     const double gmax = (tha[0] - cc) / e, gw = (tha[jw] - cc) / e;
@@ -554,35 +557,56 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     while (d < dmax && cheb(d + 1, gmax) / cheb(d + 1, gw) <= growth_cap &&
            cheb(d + 1, gmax) <= abs_cap)
       ++d;
-    double* Xa = V + nl;
-    double* Y0 = T1.as<double>();
-    double* Y1 = T2.as<double>();
-    TK_TRY(copy_cols_f64(n, ka2, Xa, k, Y0, ka2, s));
-    TK_TRY(gemm_nn_f64(n, ka2, n, 1.0 / e, M, n, Y0, ka2, -cc / e, Y0, ka2, 0.0, nullptr, 0, Y1,
-                       ka2, s));
-    st->matvecs++;
-    TK_TRY(deflate(V, k, Y1, ka2, n, nl, ka2, P.as<double>(), s));
-    for (int j = 2; j <= d; ++j) {
-      // Y0 <- (2/e) M Y1 - (2c/e) Y1 - Y0, then swap roles.
-      TK_TRY(gemm_nn_f64(n, ka2, n, 2.0 / e, M, n, Y1, ka2, -2.0 * cc / e, Y1, ka2, -1.0, Y0,
-                         ka2, Y0, ka2, s));
-      st->matvecs++;
-      TK_TRY(deflate(V, k, Y0, ka2, n, nl, ka2, P.as<double>(), s));
-      double* t = Y0; Y0 = Y1; Y1 = t;
+    // In the FP32-filter mode, switch the products to FP64 once the wanted residuals approach
+    // the FP32 noise floor.
+    if (use32) {
+      double mres = 0.0;
+      for (int i = nlock; i < ka && i < nlock + (J - nl); ++i) mres = std::max(mres, rr[i]);
+      if (mres < 1e-5 * theta1) use32 = false;
     }
-    TK_TRY(copy_cols_f64(n, ka2, Y1, ka2, Xa, k, s));
-    for (int rep = 0; rep < 2; ++rep) TK_TRY(deflate(V, k, Xa, k, n, nl, ka2, P.as<double>(), s));
-    normalize_cols_inplace<<<ka2, 256, 0, s>>>(Xa, k, n);
-    TK_LAUNCH();
-    const int qs = cholqr2(Xa, k, n, ka2, T3.as<double>(), Gk.as<double>(), R.as<double>(),
-                           Ri.as<double>(), stat.as<int>(), s);
-    if (qs != TUCKER_OK) {
-      char msg[256];
-      snprintf(msg, sizeof(msg),
-               "eigensolver: Cholesky-QR failed (n=%d J=%d k=%d outer=%d locked=%d degree=%d)",
-               n, J, k, outer, nl, d);
-      set_error_detail(msg);
-      return qs;
+    // Filter-and-orthonormalise several times per Rayleigh-Ritz step: the product of two degree-d
+    // filters grows like one of degree 2d, at the price of a Cholesky-QR2 instead of a Jacobi
+    // eigensolve.  While an outlier holds the degree at 1 these are plain power steps.
+    const int reps = d == 1 ? 4 : 2;
+    double* Xa = V + nl;
+    for (int rep = 0; rep < reps; ++rep) {
+      double* Y0 = T1.as<double>();
+      double* Y1 = T2.as<double>();
+      TK_TRY(copy_cols_f64(n, ka2, Xa, k, Y0, ka2, s));
+      if (use32)
+        TK_TRY(gemm_nn_f32a(n, ka2, n, 1.0 / e, M32, n, Y0, ka2, -cc / e, Y0, ka2, 0.0, nullptr,
+                            0, Y1, ka2, s));
+      else
+        TK_TRY(gemm_nn_f64(n, ka2, n, 1.0 / e, M, n, Y0, ka2, -cc / e, Y0, ka2, 0.0, nullptr, 0,
+                           Y1, ka2, s));
+      st->matvecs++;
+      TK_TRY(deflate(V, k, Y1, ka2, n, nl, ka2, P.as<double>(), s));
+      for (int j = 2; j <= d; ++j) {
+        // Y0 <- (2/e) M Y1 - (2c/e) Y1 - Y0, then swap roles.
+        if (use32)
+          TK_TRY(gemm_nn_f32a(n, ka2, n, 2.0 / e, M32, n, Y1, ka2, -2.0 * cc / e, Y1, ka2, -1.0,
+                              Y0, ka2, Y0, ka2, s));
+        else
+          TK_TRY(gemm_nn_f64(n, ka2, n, 2.0 / e, M, n, Y1, ka2, -2.0 * cc / e, Y1, ka2, -1.0, Y0,
+                             ka2, Y0, ka2, s));
+        st->matvecs++;
+        TK_TRY(deflate(V, k, Y0, ka2, n, nl, ka2, P.as<double>(), s));
+        double* t = Y0; Y0 = Y1; Y1 = t;
+      }
+      TK_TRY(copy_cols_f64(n, ka2, Y1, ka2, Xa, k, s));
+      for (int dd = 0; dd < 2; ++dd) TK_TRY(deflate(V, k, Xa, k, n, nl, ka2, P.as<double>(), s));
+      normalize_cols_inplace<<<ka2, 256, 0, s>>>(Xa, k, n);
+      TK_LAUNCH();
+      const int qs = cholqr2(Xa, k, n, ka2, T3.as<double>(), Gk.as<double>(), R.as<double>(),
+                             Ri.as<double>(), stat.as<int>(), s);
+      if (qs != TUCKER_OK) {
+        char msg[256];
+        snprintf(msg, sizeof(msg),
+                 "eigensolver: Cholesky-QR failed (n=%d J=%d k=%d outer=%d locked=%d degree=%d)",
+                 n, J, k, outer, nl, d);
+        set_error_detail(msg);
+        return qs;
+      }
     }
   }
   if (!done) {

@@ -63,6 +63,10 @@ int unfolding_gram_f64(const tucker_tensor_s* X, const Ordering* rows, const Ord
 int gemm_nn_f64(int m, int n, int k, double alpha, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double beta, const double* Xm, int64_t ldx, double gamma,
                 const double* Zm, int64_t ldz, double* C, int64_t ldc, cudaStream_t s);
+// The same with A in FP32 and the products and sums in FP32 (B converted on load).
+int gemm_nn_f32a(int m, int n, int k, double alpha, const float* A, int64_t lda, const double* B,
+                 int64_t ldb, double beta, const double* Xm, int64_t ldx, double gamma,
+                 const double* Zm, int64_t ldz, double* C, int64_t ldc, cudaStream_t s);
 // C[m x n] = A^T B with A: k x m, B: k x n (row-major), deterministic split-K.
 int gemm_tn_f64(int m, int n, int64_t k, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double* C, int64_t ldc, cudaStream_t s);
@@ -101,9 +105,15 @@ struct EigStats {
   bool rank_deficient = false;
 };
 // Leading J eigenvectors of the symmetric PSD n x n matrix M (device).  U0 (n x J, may be
-// NULL) warm-starts; U (n x J) and lambda (J, may be NULL) receive the result.
+// NULL) warm-starts; U (n x J) and lambda (J, may be NULL) receive the result.  Locking
+// residual |M v - theta v| <= tol * theta_1.  With M32 (an FP32 copy of M) the Chebyshev
+// filter's products run in FP32 until the residuals near the FP32 noise floor; Rayleigh-Ritz,
+// residuals and Cholesky-QR2 are always FP64.
+constexpr double EIG_TOL_FP64 = 3e-13;
+constexpr double EIG_TOL_MIXED = 1e-9;
 int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, double* lambda,
-                 cudaStream_t s, EigStats* st);
+                 cudaStream_t s, EigStats* st, const float* M32 = nullptr,
+                 double tol = EIG_TOL_FP64);
 
 // core / fit (api.cu)
 int core_from_ttmc3(const double* Y3, int I3, int J1, int J2, const double* C, int J3,

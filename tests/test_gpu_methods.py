@@ -78,9 +78,12 @@ def test_methods_ragged_subspace_path(tucker_lib, alg):
 
 
 @pytest.mark.parametrize("alg", ["hosvd", "hooi", "sp", "mp"])
-def test_exact_recovery_planted(tucker_lib, alg):
-    dims, core = (40, 36, 30), (3, 4, 2)
-    X, G, F = synth.planted_tensor(dims, core, (20, 18, 15), seed=21)
+@pytest.mark.parametrize("dims,core,support", [((40, 36, 30), (3, 4, 2), (20, 18, 15)),
+                                               ((300, 260, 240), (6, 5, 4), (40, 36, 30))])
+def test_exact_recovery_planted(tucker_lib, alg, dims, core, support):
+    """Exact multilinear rank: the small case takes the full-Jacobi eigensolver, the large one
+    the subspace iteration with a block wider than the rank of every mode matrix."""
+    X, G, F = synth.planted_tensor(dims, core, support, seed=21)
     C_raw = synth.uniform_matrix(dims[2], core[2], 5)
     T = tucker_lib.tucker_tensor_create(X.idx, X.val, X.dims)
     g = gpu_run(tucker_lib, alg, T, core, -np.inf, 3, C_raw)
