@@ -246,6 +246,27 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
+def profile_leg(args):
+    """One precision leg only (warm-up + timed steps), for profiler captures."""
+    import torch
+    from paper_0711_2023_gb300 import build, tucker as tk
+    build.build()
+    X, C_raw = make_inputs(0)
+    d_idx = torch.from_numpy(X.idx).cuda()
+    d_val = torch.from_numpy(X.val).cuda()
+    l2buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    dev_tensor = lambda: tk.tucker_tensor_create(d_idx, d_val, X.dims)  # noqa: E731
+    for _ in range(args.warmup):
+        run_job(tk, dev_tensor, C_raw, "device", args.profile_leg)
+    ms, passes, fits, launches, clk, prof = timed_region(
+        tk, torch, 1, 0, args.steps, dev_tensor, C_raw, l2buf, args.profile_leg)
+    print(json.dumps({"leg": args.profile_leg, "value": passes / (ms / 1e3), "unit": "sweeps/s",
+                      "ms_per_step": ms / args.steps, "gpu_launches": launches, "fits": fits,
+                      "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                                      "share": round(v["ms"] / ms, 4)} for k, v in prof.items()}}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -253,11 +274,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-leg", choices=["fp64", "mixed"], default=None,
+                    help="run only warm-up + timed steps of one precision leg (for ncu captures) "
+                         "and print a short summary line")
     args = ap.parse_args()
 
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.profile_leg:
+        profile_leg(args)
         return
 
     import torch

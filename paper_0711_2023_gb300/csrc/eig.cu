@@ -1,19 +1,22 @@
 // Leading-J eigenvectors of a symmetric positive semi-definite matrix M (n x n, FP64): the
 // "J_n leading eigenvectors of ..." step of every method (Figures HO-SVD3, hooi3, sp3, mp3).
 //
-// Method (all FP64):
+// Method:
 //   * small n: cyclic two-sided Jacobi on M itself (Golub & Van Loan, Sec. 8.5, parallel
-//     round-robin ordering) in one cooperative launch;
-//   * otherwise block subspace iteration on k = J + p columns with
-//       - Rayleigh-Ritz: H = V^T M V, eigenpairs of H by the same Jacobi kernel, V <- V Q;
-//       - locking: leading Ritz pairs with residual |M v - theta v| <= tol * theta_1 are
-//         frozen; later products are projected against them;
-//       - Chebyshev filtering (Zhou & Saad's filtered subspace iteration): p_d(M) with the
-//         unwanted interval [0, theta_k] mapped to [-1, 1]; each column is rescaled by
-//         1/T_d of its Ritz value and d is capped so that no column outgrows the last wanted
-//         one by more than a fixed factor, which keeps the block well conditioned;
-//       - Cholesky-QR2 orthonormalisation (R = chol(V^T V), V <- V R^-1, twice), with a
-//         shifted first pass if the Gram matrix is not numerically positive definite.
+//     round-robin ordering) in one cooperative launch, FP64;
+//   * otherwise block subspace iteration on k = J + max(16, J/2) columns:
+//       - four power steps from the start block (warm start: the previous pass's factor);
+//       - Rayleigh-Ritz (FP64): H = V^T M V, eigenpairs of H by the same Jacobi kernel,
+//         V <- V Q; residuals |M v - theta v| in FP64;
+//       - locking: leading Ritz pairs with residual <= tol * theta_1 are frozen and removed
+//         from the filter's operator, M_d = M - L diag(theta_L) L^T;
+//       - Chebyshev filtering (Zhou & Saad's filtered subspace iteration): p_d(M_d) with the
+//         unwanted interval [0, theta_k] mapped to [-1, 1], the degree d capped so that the
+//         block stays well conditioned, two filter applications per Rayleigh-Ritz step (four
+//         power steps while an outlier eigenvalue pins d to 1); optionally the filter's
+//         products run in FP32 until the residuals near the FP32 noise floor;
+//       - Cholesky-QR2 orthonormalisation in FP64 (R = chol(V^T V), V <- V R^-1, twice), with
+//         a shifted pass when the Gram matrix is not numerically positive definite.
 //   The returned columns are sorted by eigenvalue (largest first) and sign-normalised: the
 //   entry of largest magnitude in each column is positive.
 #include <math.h>
@@ -44,6 +47,40 @@ struct JacobiArgs {
   int* sweeps_out;
 };
 
+struct Rot {
+  double c, s, np, nq;
+  bool on;
+};
+
+// Symmetric 2x2 Schur decomposition (Golub & Van Loan, Algorithm 8.4.1): the rotation that
+// zeroes a_pq.  Kept out of line so every thread computing the same pair gets the same bits.
+__device__ __noinline__ Rot sym_schur2(double app, double aqq, double apq, bool active,
+                                       double tol, double abs_tol) {
+  Rot r{1.0, 0.0, app, aqq, false};
+  if (active && fabs(apq) > abs_tol && fabs(apq) > tol * sqrt(fabs(app * aqq))) {
+    const double tau = (aqq - app) / (2.0 * apq);
+    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    r.c = 1.0 / sqrt(1.0 + t * t);
+    r.s = t * r.c;
+    r.np = app - t * apq;
+    r.nq = aqq + t * apq;
+    r.on = true;
+  }
+  return r;
+}
+
+__device__ __forceinline__ void pair_of(int I, int r, int m, int* p, int* q) {
+  const int a = rr_index(I, r, m), b = rr_index(m - 1 - I, r, m);
+  *p = min(a, b);
+  *q = max(a, b);
+}
+
+// Cyclic two-sided Jacobi, round-robin ordering: in round r the m/2 disjoint pairs are rotated
+// at once.  Work items of a round: the 2x2 blocks (I <= K) of A' = J^T A J (double-buffered),
+// then the (row, pair) items of Q <- Q J.  Each block first issues the loads of its first work
+// item, then computes the round's rotations into shared memory (one thread per pair, from the
+// diagonal 2x2 blocks of the current A) while those loads are in flight, then applies them; a
+// round ends with one grid barrier.
 __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
   extern __shared__ double sh[];
   const int m = g.m, h = m / 2;
@@ -66,63 +103,79 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
   __syncthreads();
   const double abs_tol = 1e-17 * normA_s + 1e-300;
   const int64_t ntri = (int64_t)h * (h + 1) / 2;
+  const int64_t nwork = ntri + (int64_t)m * h;
   unsigned int epoch = 0;
   int sweep = 0;
   bool alive = true;
   for (; sweep < g.max_sweeps && alive; ++sweep) {
     for (int r = 0; r < m - 1 && alive; ++r) {
-      for (int i = threadIdx.x; i < h; i += blockDim.x) {
-        const int a = rr_index(i, r, m), b = rr_index(m - 1 - i, r, m);
-        const int p = min(a, b), q = max(a, b);
-        const double app = Acur[(int64_t)p * m + p], aqq = Acur[(int64_t)q * m + q];
-        const double apq = Acur[(int64_t)p * m + q];
-        double c = 1.0, s = 0.0, np = app, nq = aqq;
-        if (q < g.mreal && fabs(apq) > abs_tol && fabs(apq) > g.tol * sqrt(fabs(app * aqq))) {
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
-          np = app - t * apq;
-          nq = aqq + t * apq;
-          if (blockIdx.x == 0) atomicAdd(&g.rot[sweep], 1u);
+      bool first = true;
+      for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < nwork || first; t0 += gsize) {
+        const int64_t t = t0 + threadIdx.x;
+        // ---- decode the item and issue its loads -------------------------------------------
+        int I = 0, K = 0, row = -1, p = 0, q = 0, u = 0, v = 0;
+        double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+        const bool valid = t < nwork;
+        const bool is_a = valid && t < ntri;
+        if (is_a) {
+          K = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+          while ((int64_t)K * (K + 1) / 2 > t) --K;
+          while ((int64_t)(K + 1) * (K + 2) / 2 <= t) ++K;
+          I = (int)(t - (int64_t)K * (K + 1) / 2);
+          pair_of(I, r, m, &p, &q);
+          if (I != K) {
+            pair_of(K, r, m, &u, &v);
+            x0 = Acur[(int64_t)p * m + u];
+            x1 = Acur[(int64_t)p * m + v];
+            x2 = Acur[(int64_t)q * m + u];
+            x3 = Acur[(int64_t)q * m + v];
+          }
+        } else if (valid) {
+          const int64_t t2 = t - ntri;
+          row = (int)(t2 / h);
+          I = (int)(t2 % h);
+          pair_of(I, r, m, &p, &q);
+          x0 = g.Q[(int64_t)row * m + p];
+          x1 = g.Q[(int64_t)row * m + q];
         }
-        cs[i] = c; sn[i] = s; dp[i] = np; dq[i] = nq; pi[i] = p; qi[i] = q;
-      }
-      __syncthreads();
-      for (int64_t t = gtid; t < ntri; t += gsize) {
-        int K = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((int64_t)K * (K + 1) / 2 > t) --K;
-        while ((int64_t)(K + 1) * (K + 2) / 2 <= t) ++K;
-        const int I = (int)(t - (int64_t)K * (K + 1) / 2);
-        const int p = pi[I], q = qi[I];
-        if (I == K) {
-          Anext[(int64_t)p * m + p] = dp[I];
-          Anext[(int64_t)q * m + q] = dq[I];
-          Anext[(int64_t)p * m + q] = 0.0;
-          Anext[(int64_t)q * m + p] = 0.0;
-        } else {
-          const int u = pi[K], v = qi[K];
-          const double c1 = cs[I], s1 = sn[I], c2 = cs[K], s2 = sn[K];
-          const double apu = Acur[(int64_t)p * m + u], apv = Acur[(int64_t)p * m + v];
-          const double aqu = Acur[(int64_t)q * m + u], aqv = Acur[(int64_t)q * m + v];
-          const double rpu = c1 * apu - s1 * aqu, rpv = c1 * apv - s1 * aqv;
-          const double rqu = s1 * apu + c1 * aqu, rqv = s1 * apv + c1 * aqv;
-          const double bpu = c2 * rpu - s2 * rpv, bpv = s2 * rpu + c2 * rpv;
-          const double bqu = c2 * rqu - s2 * rqv, bqv = s2 * rqu + c2 * rqv;
-          Anext[(int64_t)p * m + u] = bpu; Anext[(int64_t)u * m + p] = bpu;
-          Anext[(int64_t)p * m + v] = bpv; Anext[(int64_t)v * m + p] = bpv;
-          Anext[(int64_t)q * m + u] = bqu; Anext[(int64_t)u * m + q] = bqu;
-          Anext[(int64_t)q * m + v] = bqv; Anext[(int64_t)v * m + q] = bqv;
+        // ---- the round's rotations (once per block) ------------------------------------------
+        if (first) {
+          for (int i = threadIdx.x; i < h; i += blockDim.x) {
+            int pp, qq;
+            pair_of(i, r, m, &pp, &qq);
+            const Rot R = sym_schur2(Acur[(int64_t)pp * m + pp], Acur[(int64_t)qq * m + qq],
+                                     Acur[(int64_t)pp * m + qq], qq < g.mreal, g.tol, abs_tol);
+            if (R.on && blockIdx.x == 0) atomicAdd(&g.rot[sweep], 1u);
+            cs[i] = R.c; sn[i] = R.s; dp[i] = R.np; dq[i] = R.nq; pi[i] = pp; qi[i] = qq;
+          }
+          __syncthreads();
+          first = false;
         }
-      }
-      for (int64_t t = gtid; t < (int64_t)m * h; t += gsize) {
-        const int row = (int)(t / h), I = (int)(t % h);
-        const double c = cs[I], s = sn[I];
-        if (s == 0.0) continue;
-        double* Qr = g.Q + (int64_t)row * m;
-        const double qp = Qr[pi[I]], qq = Qr[qi[I]];
-        Qr[pi[I]] = c * qp - s * qq;
-        Qr[qi[I]] = s * qp + c * qq;
+        // ---- apply ---------------------------------------------------------------------------
+        if (is_a) {
+          if (I == K) {
+            Anext[(int64_t)p * m + p] = dp[I];
+            Anext[(int64_t)q * m + q] = dq[I];
+            Anext[(int64_t)p * m + q] = 0.0;
+            Anext[(int64_t)q * m + p] = 0.0;
+          } else {
+            const double c1 = cs[I], s1 = sn[I], c2 = cs[K], s2 = sn[K];
+            const double rpu = c1 * x0 - s1 * x2, rpv = c1 * x1 - s1 * x3;
+            const double rqu = s1 * x0 + c1 * x2, rqv = s1 * x1 + c1 * x3;
+            const double bpu = c2 * rpu - s2 * rpv, bpv = s2 * rpu + c2 * rpv;
+            const double bqu = c2 * rqu - s2 * rqv, bqv = s2 * rqu + c2 * rqv;
+            Anext[(int64_t)p * m + u] = bpu; Anext[(int64_t)u * m + p] = bpu;
+            Anext[(int64_t)p * m + v] = bpv; Anext[(int64_t)v * m + p] = bpv;
+            Anext[(int64_t)q * m + u] = bqu; Anext[(int64_t)u * m + q] = bqu;
+            Anext[(int64_t)q * m + v] = bqv; Anext[(int64_t)v * m + q] = bqv;
+          }
+        } else if (valid) {
+          const double c = cs[I], s = sn[I];
+          if (s != 0.0) {
+            g.Q[(int64_t)row * m + p] = c * x0 - s * x1;
+            g.Q[(int64_t)row * m + q] = s * x0 + c * x1;
+          }
+        }
       }
       alive = grid_barrier(g.bar, gridDim.x, &epoch, g.status);
       double* tmp = Acur; Acur = Anext; Anext = tmp;
@@ -304,6 +357,25 @@ __global__ void normalize_cols_inplace(double* V, int64_t ld, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) V[(int64_t)i * ld + j] *= inv;
 }
 
+// LS = L diag(lam) (n x nl, ld nl) and Lt = L^T (nl x n) from the first nl columns L of V.
+__global__ void scaled_transpose(const double* __restrict__ V, int64_t ldv, int n, int nl,
+                                 const double* __restrict__ lam, double* __restrict__ LS,
+                                 double* __restrict__ Lt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * nl) return;
+  const int64_t i = t / nl, l = t % nl;
+  const double v = V[i * ldv + l];
+  LS[i * nl + l] = v * lam[l];
+  Lt[l * n + i] = v;
+}
+
+// y += a * x over n contiguous elements.
+__global__ void add_scaled(double* __restrict__ y, const double* __restrict__ x, double a,
+                           int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] = fma(a, x[t], y[t]);
+}
+
 // Columns [c0, c1) of V (n x ld) from a counter-based hash: uniform in [-1, 1).
 __global__ void random_cols(double* V, int64_t ld, int n, int c0, int c1, uint64_t seed) {
   const int64_t w = c1 - c0;
@@ -377,7 +449,7 @@ int jacobi_eig(const double* A, int mreal, int64_t lda, double* Qout, double* ev
   if (smem > 48 * 1024)
     TK_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-  const int work = std::max(h * (h + 1) / 2, m * h);
+  const int work = h * (h + 1) / 2 + m * h;
   const int grid = cooperative_grid(std::min(work, 1 << 22), smem);
   void* args[] = {&g};
   {
@@ -477,6 +549,14 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   const int max_outer = 120, dmax = 24;
   const double growth_cap = 1e4, abs_cap = 1e8;
   Buf Vb, T1, T2, T3, H, Qh, evh, Gk, R, Ri, P, rn, stat;
+  Buf Md, Md32, LS, Lt, lamd;  // deflated filter operator and its factors
+  TK_TRY(Md.alloc(sizeof(double) * n * n, s));
+  if (M32) TK_TRY(Md32.alloc(sizeof(float) * n * n, s));
+  TK_TRY(LS.alloc(sizeof(double) * n * k, s));
+  TK_TRY(Lt.alloc(sizeof(double) * n * k, s));
+  TK_TRY(lamd.alloc(sizeof(double) * k, s));
+  const double* Mf = M;    // operator of the filter: M, then M with the locked pairs removed
+  const float* Mf32 = M32;
   const size_t nk = sizeof(double) * (size_t)n * k;
   TK_TRY(Vb.alloc(nk, s));
   TK_TRY(T1.alloc(nk, s));
@@ -502,6 +582,28 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   TK_LAUNCH();
   TK_TRY(cholqr2(V, k, n, k, T1.as<double>(), Gk.as<double>(), R.as<double>(), Ri.as<double>(),
                  stat.as<int>(), s));
+  // Power steps before the first Rayleigh-Ritz solve (which on a random or stale block would
+  // buy nothing): V <- orth(normalise(M V) + 1e-3 V).  The small multiple of V keeps the block
+  // of full rank when M has fewer than k nonzero eigenvalues.
+  for (int rep = 0; rep < 4; ++rep) {
+    double* W = T1.as<double>();
+    if (use32)
+      TK_TRY(gemm_nn_f32a(n, k, n, 1.0, M32, n, V, k, 0.0, nullptr, 0, 0.0, nullptr, 0, W, k, s));
+    else
+      TK_TRY(gemm_nn_f64(n, k, n, 1.0, M, n, V, k, 0.0, nullptr, 0, 0.0, nullptr, 0, W, k, s));
+    st->matvecs++;
+    normalize_cols_inplace<<<k, 256, 0, s>>>(W, k, n);
+    TK_LAUNCH();
+    add_scaled<<<ceil_div((int64_t)n * k, 256), 256, 0, s>>>(W, V, 1e-3, (int64_t)n * k);
+    TK_LAUNCH();
+    TK_TRY(copy_cols_f64(n, k, W, k, V, k, s));
+    const int qs = cholqr2(V, k, n, k, T2.as<double>(), Gk.as<double>(), R.as<double>(),
+                           Ri.as<double>(), stat.as<int>(), s);
+    if (qs != TUCKER_OK) {
+      set_error_detail("eigensolver: Cholesky-QR failed in the initial power steps");
+      return qs;
+    }
+  }
 
   int nl = 0;
   double theta1 = 0.0;
@@ -541,6 +643,23 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     }
     nl += nlock;
     if (nl >= J) { done = true; break; }
+    if (nlock > 0) {
+      // Filter operator with the locked pairs removed: Md = M - L diag(theta_L) L^T.  Their
+      // eigenvalues drop to ~0, inside the damped interval, so the filter needs no projection
+      // at every step (only the final one below).
+      TK_CUDA(cudaMemcpyAsync(lamd.p, locked_theta.data(), sizeof(double) * nl,
+                              cudaMemcpyHostToDevice, s));
+      scaled_transpose<<<ceil_div((int64_t)n * nl, 256), 256, 0, s>>>(V, k, n, nl,
+                                                                    lamd.as<double>(),
+                                                                    LS.as<double>(),
+                                                                    Lt.as<double>());
+      TK_LAUNCH();
+      TK_TRY(gemm_nn_f64(n, n, nl, -1.0, LS.as<double>(), nl, Lt.as<double>(), n, 1.0, M, n, 0.0,
+                         nullptr, 0, Md.as<double>(), n, s));
+      if (M32) TK_TRY(f64_to_f32(Md.as<double>(), Md32.as<float>(), (int64_t)n * n, s));
+      Mf = Md.as<double>();
+      Mf32 = M32 ? Md32.as<float>() : nullptr;
+    }
     // Chebyshev filter on the remaining active columns.
     const int ka2 = k - nl;
     const double* tha = th.data() + nlock;
@@ -574,23 +693,21 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
       double* Y1 = T2.as<double>();
       TK_TRY(copy_cols_f64(n, ka2, Xa, k, Y0, ka2, s));
       if (use32)
-        TK_TRY(gemm_nn_f32a(n, ka2, n, 1.0 / e, M32, n, Y0, ka2, -cc / e, Y0, ka2, 0.0, nullptr,
+        TK_TRY(gemm_nn_f32a(n, ka2, n, 1.0 / e, Mf32, n, Y0, ka2, -cc / e, Y0, ka2, 0.0, nullptr,
                             0, Y1, ka2, s));
       else
-        TK_TRY(gemm_nn_f64(n, ka2, n, 1.0 / e, M, n, Y0, ka2, -cc / e, Y0, ka2, 0.0, nullptr, 0,
+        TK_TRY(gemm_nn_f64(n, ka2, n, 1.0 / e, Mf, n, Y0, ka2, -cc / e, Y0, ka2, 0.0, nullptr, 0,
                            Y1, ka2, s));
       st->matvecs++;
-      TK_TRY(deflate(V, k, Y1, ka2, n, nl, ka2, P.as<double>(), s));
       for (int j = 2; j <= d; ++j) {
         // Y0 <- (2/e) M Y1 - (2c/e) Y1 - Y0, then swap roles.
         if (use32)
-          TK_TRY(gemm_nn_f32a(n, ka2, n, 2.0 / e, M32, n, Y1, ka2, -2.0 * cc / e, Y1, ka2, -1.0,
+          TK_TRY(gemm_nn_f32a(n, ka2, n, 2.0 / e, Mf32, n, Y1, ka2, -2.0 * cc / e, Y1, ka2, -1.0,
                               Y0, ka2, Y0, ka2, s));
         else
-          TK_TRY(gemm_nn_f64(n, ka2, n, 2.0 / e, M, n, Y1, ka2, -2.0 * cc / e, Y1, ka2, -1.0, Y0,
+          TK_TRY(gemm_nn_f64(n, ka2, n, 2.0 / e, Mf, n, Y1, ka2, -2.0 * cc / e, Y1, ka2, -1.0, Y0,
                              ka2, Y0, ka2, s));
         st->matvecs++;
-        TK_TRY(deflate(V, k, Y0, ka2, n, nl, ka2, P.as<double>(), s));
         double* t = Y0; Y0 = Y1; Y1 = t;
       }
       TK_TRY(copy_cols_f64(n, ka2, Y1, ka2, Xa, k, s));

@@ -110,7 +110,7 @@ struct EigStats {
 // filter's products run in FP32 until the residuals near the FP32 noise floor; Rayleigh-Ritz,
 // residuals and Cholesky-QR2 are always FP64.
 constexpr double EIG_TOL_FP64 = 3e-13;
-constexpr double EIG_TOL_MIXED = 1e-9;
+constexpr double EIG_TOL_MIXED = 1e-6;
 int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, double* lambda,
                  cudaStream_t s, EigStats* st, const float* M32 = nullptr,
                  double tol = EIG_TOL_FP64);
