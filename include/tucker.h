@@ -138,6 +138,18 @@ int tucker_slice_proj(tucker_tensor X, int32_t n, int32_t m, const double* d_Um,
 int tucker_gram(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2, int32_t rows,
                 double* d_M, void* stream);
 
+/* Allocation-free tucker_gram (the paper has no counterpart: this serves callers that cannot
+ * let a library allocate device memory while they run, such as serving processes that reserve
+ * all device memory in their own pool, or callers that must avoid the implicit synchronisation
+ * cudaMalloc/cudaFree can cause).  Same arguments and result as tucker_gram; the split-K
+ * workspace is one fixed array of 2^21 doubles (16 MiB) that every GPU loading the library
+ * holds until exit, so rows * rows must be <= 2^21 (rows <= 1448), else TUCKER_EINVAL.  The
+ * first call on a device looks up the array's address (cudaGetSymbolAddress): make it before
+ * any stream capture.  Calls share the array: calls that overlap on the GPU race; order them
+ * on one stream. */
+int tucker_gram_noalloc(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2,
+                        int32_t rows, double* d_M, void* stream);
+
 /* ---- mixed-precision steps (TUCKER_MIXED form) ---------------------------------------------
  * BF16 matrices are passed as uint16_t bit patterns.  A "split" matrix Y is stored as two
  * BF16 matrices hi = bf16(y), lo = bf16(y - hi), row-major with row stride ld (elements, a

@@ -80,6 +80,8 @@ _SIGS = {
                                           c_void_p, c_void_p, c_int64, c_void_p]),
     "tucker_gram_bf16x3": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p,
                                      c_int64, c_int64, c_int32, c_void_p, c_void_p]),
+    "tucker_gram_noalloc": (c_int32, [c_void_p, c_int64, c_void_p, c_int64, c_int32, c_void_p,
+                                      c_void_p]),
     "tucker_profile_enable": (None, [c_int32]),
     "tucker_profile_query": (c_int32, [c_char_p, POINTER(c_int64), POINTER(c_double),
                                        POINTER(c_double), POINTER(c_double)]),
@@ -332,6 +334,23 @@ def tucker_gram(Y1, Y2=None):
     _check(_lib().tucker_gram(_dptr(Y1), Y1.shape[1], _dptr(Y2) if Y2 is not None else None,
                               Y2.shape[1] if Y2 is not None else 0, rows, _dptr(M), _stream()),
            "tucker_gram")
+    return M
+
+
+def tucker_gram_noalloc(Y1, Y2=None, M=None):
+    """tucker_gram through the allocation-free entry point.  The output M (rows x rows, float64,
+    CUDA) may be passed in; the library itself allocates nothing for this call."""
+    torch = _torch()
+    Y1 = _dev_f64(Y1)
+    rows = Y1.shape[0]
+    if M is None:
+        M = torch.empty((rows, rows), dtype=torch.float64, device="cuda")
+    if Y2 is not None:
+        Y2 = _dev_f64(Y2)
+    _check(_lib().tucker_gram_noalloc(_dptr(Y1), Y1.shape[1],
+                                      _dptr(Y2) if Y2 is not None else None,
+                                      Y2.shape[1] if Y2 is not None else 0, rows, _dptr(M),
+                                      _stream()), "tucker_gram_noalloc")
     return M
 
 
