@@ -103,6 +103,18 @@ int tucker_hooi(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tu
 int tucker_sp(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out);
 int tucker_mp(tucker_tensor X, const int32_t J[3], const tucker_opts* opts, tucker_result* out);
 
+/* ---- batched form -------------------------------------------------------------------------
+ * HOOI (Figure hooi3) or MP (Figure mp3) on `count` independent tensors Xs[t] with core sizes
+ * J[3t .. 3t+2]; results in out[t] (each with its own buffers and `where`).  opts applies to
+ * all tensors (its init[] must be NULL).  The tensors' decompositions run concurrently on the
+ * GPU (a pool of host threads, one non-blocking stream each, on the calling thread's device);
+ * every ordering of every tensor is built first on opts->stream.  Each result equals what the
+ * single-tensor call returns.  Returns the first failing tensor's status (lowest index). */
+int tucker_hooi_batched(int32_t count, const tucker_tensor* Xs, const int32_t* J,
+                        const tucker_opts* opts, tucker_result* out);
+int tucker_mp_batched(int32_t count, const tucker_tensor* Xs, const int32_t* J,
+                      const tucker_opts* opts, tucker_result* out);
+
 const char* tucker_strerror(int status);
 /* Text of the last CUDA failure seen by the calling thread (empty if none). */
 const char* tucker_last_error_detail(void);

@@ -12,7 +12,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -32,14 +35,38 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 void set_error_detail(const char* msg) { g_last_error = msg; }
 
 int num_sms() {
-  static int n = 0;
+  static std::atomic<int> cached{0};
+  int n = cached.load(std::memory_order_relaxed);
   if (n == 0) {
-    int dev = 0;
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    n = v > 0 ? v : 1;
+    cached.store(n, std::memory_order_relaxed);
   }
   return n;
+}
+
+namespace {
+// Work buffers come from the device's default stream-ordered pool.  By default the pool hands
+// freed memory back to the driver at every synchronisation, so the next allocation has to map
+// it again; the library synchronises often (the eigensolver reads Ritz values back), so keep
+// freed blocks in the pool instead.
+std::mutex g_pool_mu;
+bool g_pool_ready[64] = {};
+}  // namespace
+
+void keep_pool_memory() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pool_ready[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  g_pool_ready[dev] = true;
 }
 
 int ordering_slot(int n, int m, int o) {
@@ -450,12 +477,82 @@ int run_method(Method method, tucker_tensor_s* X, const int32_t J[3], const tuck
   return finish(r, out);
 }
 
+// ----------------------------------------------------------------------------------------------
+// Batched driver: many independent tensors.  Every ordering (with its fiber map and FP32
+// values) of every tensor is built first, on the caller's stream, so that the worker threads
+// only read the handles; then a pool of host threads, each with its own non-blocking stream,
+// runs the tensors' decompositions concurrently on the GPU.
+// ----------------------------------------------------------------------------------------------
+constexpr int BATCH_STREAMS = 16;
+
+int prepare_all_orderings(tucker_tensor_s* X, bool mixed, cudaStream_t s) {
+  for (int n = 0; n < 3; ++n)
+    for (int m = 0; m < 3; ++m) {
+      if (m == n) continue;
+      const int o = 3 - n - m;
+      Ordering* ord;
+      TK_TRY(ensure_ordering(X, n, m, o, s, &ord));
+      TK_TRY(ensure_fiber_map(X, ord, s));
+      if (mixed) TK_TRY(ensure_val_f32(X, ord, s));
+    }
+  return TUCKER_OK;
+}
+
+int run_batched(Method method, int32_t count, const tucker_tensor* Xs, const int32_t* J,
+                const tucker_opts* opts, tucker_result* out) {
+  if (count < 0 || (count > 0 && (!Xs || !J || !out))) return TUCKER_EINVAL;
+  if (count == 0) return TUCKER_OK;
+  const tucker_opts base = opts ? *opts : default_opts();
+  if (base.init[0] || base.init[1] || base.init[2]) return TUCKER_EINVAL;  // no per-tensor starts
+  cudaStream_t s0 = (cudaStream_t)base.stream;
+  const bool mixed = base.precision == TUCKER_MIXED;
+  for (int t = 0; t < count; ++t) {
+    if (!Xs[t]) return TUCKER_EINVAL;
+    TK_TRY(prepare_all_orderings(Xs[t], mixed, s0));
+  }
+  TK_CUDA(cudaStreamSynchronize(s0));
+  int dev = 0;
+  TK_CUDA(cudaGetDevice(&dev));
+  const int nthreads = std::min<int>(count, BATCH_STREAMS);
+  std::vector<cudaStream_t> streams(nthreads, nullptr);
+  for (int i = 0; i < nthreads; ++i)
+    TK_CUDA(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking));
+  std::vector<int> status(count, TUCKER_OK);
+  std::vector<std::thread> pool;
+  for (int i = 0; i < nthreads; ++i)
+    pool.emplace_back([&, i]() {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        for (int t = i; t < count; t += nthreads) status[t] = TUCKER_ECUDA;
+        return;
+      }
+      tucker_opts o = base;
+      o.stream = streams[i];
+      for (int t = i; t < count; t += nthreads)
+        status[t] = run_method(method, Xs[t], J + 3 * (int64_t)t, &o, &out[t]);
+    });
+  for (auto& th : pool) th.join();
+  for (auto st : streams) cudaStreamDestroy(st);
+  for (int t = 0; t < count; ++t)
+    if (status[t] != TUCKER_OK) return status[t];
+  return TUCKER_OK;
+}
+
 }  // namespace
 }  // namespace tk
 
 using namespace tk;
 
 extern "C" {
+
+int tucker_hooi_batched(int32_t count, const tucker_tensor* Xs, const int32_t* J,
+                        const tucker_opts* opts, tucker_result* out) {
+  return run_batched(Method::HOOI, count, Xs, J, opts, out);
+}
+
+int tucker_mp_batched(int32_t count, const tucker_tensor* Xs, const int32_t* J,
+                      const tucker_opts* opts, tucker_result* out) {
+  return run_batched(Method::MP, count, Xs, J, opts, out);
+}
 
 const char* tucker_strerror(int status) {
   switch (status) {

@@ -36,6 +36,7 @@ namespace tk {
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 void set_error_detail(const char* msg);
+void keep_pool_memory();  // once per device: freed work buffers stay in the stream pool
 void count_launch();
 
 // Records CUDA events around its lifetime on `s` when profiling is enabled
@@ -76,6 +77,7 @@ struct Buf {
   Buf& operator=(const Buf&) = delete;
   ~Buf() { release(); }
   int alloc(size_t nbytes, cudaStream_t stream) {
+    keep_pool_memory();
     release();
     s = stream;
     bytes = nbytes;

@@ -251,7 +251,7 @@ __global__ void scale_kernel(int64_t n, double alpha, double* x) {
 int choose_splits(int tiles, int64_t k) {
   const int target = 3 * num_sms();
   int splits = (target + tiles - 1) / tiles;
-  const int64_t maxs = (k + 127) / 128;
+  const int64_t maxs = (k + 31) / 32;  // K slices of at least 32
   if (splits > maxs) splits = (int)maxs;
   if (splits < 1) splits = 1;
   return splits;
@@ -318,6 +318,8 @@ int gemm_nn_f32a(int m, int n, int k, double alpha, const float* A, int64_t lda,
 int gemm_tn_f64(int m, int n, int64_t k, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
   if (m <= 0 || n <= 0) return TUCKER_OK;
+  ProfScope prof("gemm_tn_f64", s, 2.0 * m * n * (double)k,
+                 8.0 * ((double)m * k + (double)k * n + (double)m * n));
   const int tiles = ceil_div(m, BM) * ceil_div(n, BN);
   const int splits = choose_splits(tiles, k);
   int64_t kchunk = (k + splits - 1) / splits;

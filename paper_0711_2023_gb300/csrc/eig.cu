@@ -45,7 +45,15 @@ struct JacobiArgs {
   unsigned* rot;      // rotations applied per sweep [max_sweeps]
   int* status;
   int* sweeps_out;
+  int cluster;        // 1: the grid is one thread-block cluster, rounds end with its barrier
 };
+
+// End of a Jacobi round for a grid that is a single cluster: the hardware cluster barrier
+// (release/acquire at cluster scope orders the round's global-memory writes).
+__device__ __forceinline__ void cluster_round_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 struct Rot {
   double c, s, np, nq;
@@ -57,10 +65,12 @@ struct Rot {
 __device__ __noinline__ Rot sym_schur2(double app, double aqq, double apq, bool active,
                                        double tol, double abs_tol) {
   Rot r{1.0, 0.0, app, aqq, false};
-  if (active && fabs(apq) > abs_tol && fabs(apq) > tol * sqrt(fabs(app * aqq))) {
-    const double tau = (aqq - app) / (2.0 * apq);
-    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-    r.c = 1.0 / sqrt(1.0 + t * t);
+  // The threshold compares squares: FP64 square roots and divisions are long instruction
+  // sequences on this part and this runs on every round's critical path.
+  if (active && fabs(apq) > abs_tol && apq * apq > tol * tol * fabs(app * aqq)) {
+    const double tau = (aqq - app) * (0.5 / apq);
+    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
+    r.c = rsqrt(fma(t, t, 1.0));
     r.s = t * r.c;
     r.np = app - t * apq;
     r.nq = aqq + t * apq;
@@ -81,7 +91,9 @@ __device__ __forceinline__ void pair_of(int I, int r, int m, int* p, int* q) {
 // item, then computes the round's rotations into shared memory (one thread per pair, from the
 // diagonal 2x2 blocks of the current A) while those loads are in flight, then applies them; a
 // round ends with one grid barrier.
-__global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
+constexpr int CLUSTER_JACOBI_MAX_M = 128;
+
+__global__ void __launch_bounds__(512) jacobi_kernel(JacobiArgs g) {
   extern __shared__ double sh[];
   const int m = g.m, h = m / 2;
   double* cs = sh;
@@ -118,7 +130,8 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
         const bool valid = t < nwork;
         const bool is_a = valid && t < ntri;
         if (is_a) {
-          K = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+          // triangular index from an FP32 estimate, corrected exactly in integers below
+          K = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
           while ((int64_t)K * (K + 1) / 2 > t) --K;
           while ((int64_t)(K + 1) * (K + 2) / 2 <= t) ++K;
           I = (int)(t - (int64_t)K * (K + 1) / 2);
@@ -177,7 +190,11 @@ __global__ void __launch_bounds__(256) jacobi_kernel(JacobiArgs g) {
           }
         }
       }
-      alive = grid_barrier(g.bar, gridDim.x, &epoch, g.status);
+      if (g.cluster) {
+        cluster_round_barrier();
+      } else {
+        alive = grid_barrier(g.bar, gridDim.x, &epoch, g.status);
+      }
       double* tmp = Acur; Acur = Anext; Anext = tmp;
     }
     if (!alive) break;
@@ -277,6 +294,7 @@ chol_inv_kernel(const double* __restrict__ G, int k, double shift, double* __res
     R[t] = (c >= r) ? G[t] + (r == c ? shift : 0.0) : 0.0;
   }
   __syncthreads();
+  __shared__ double inv_s;
   for (int j = 0; j < k; ++j) {
     const double d = R[(int64_t)j * k + j];
     if (!(d > 0.0)) {
@@ -284,10 +302,11 @@ chol_inv_kernel(const double* __restrict__ G, int k, double shift, double* __res
       __syncthreads();
       break;
     }
-    const double rjj = sqrt(d);
+    if (threadIdx.x == 0) inv_s = rsqrt(d);  // one thread: FP64 rsqrt is a long sequence
     __syncthreads();
+    const double inv = inv_s;
     for (int c = j + threadIdx.x; c < k; c += blockDim.x)
-      R[(int64_t)j * k + c] = (c == j) ? rjj : R[(int64_t)j * k + c] / rjj;
+      R[(int64_t)j * k + c] = (c == j) ? d * inv : R[(int64_t)j * k + c] * inv;
     __syncthreads();
     const int rem = k - j - 1;
     for (int64_t t = threadIdx.x; t < (int64_t)rem * rem; t += blockDim.x) {
@@ -300,15 +319,85 @@ chol_inv_kernel(const double* __restrict__ G, int k, double shift, double* __res
     if (threadIdx.x == 0) atomicOr(status, DEV_CHOL_BREAKDOWN);
     return;
   }
-  // Column c of R^{-1} by back substitution (one thread per column).
+  // Column c of R^{-1} by back substitution (one thread per column), with the reciprocal
+  // diagonal formed once per row.
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
     for (int i = 0; i < k; ++i) Rinv[(int64_t)i * k + c] = 0.0;
     Rinv[(int64_t)c * k + c] = 1.0 / R[(int64_t)c * k + c];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
     for (int i = c - 1; i >= 0; --i) {
       double s = 0.0;
       for (int l = i + 1; l <= c; ++l) s = fma(R[(int64_t)i * k + l], Rinv[(int64_t)l * k + c], s);
-      Rinv[(int64_t)i * k + c] = -s / R[(int64_t)i * k + i];
+      Rinv[(int64_t)i * k + c] = -s * Rinv[(int64_t)i * k + i];
     }
+  }
+}
+
+// The same factorisation with R and R^{-1} in shared memory (k <= CHOL_SMEM_MAX_K).  The
+// inverse is built row by row from the bottom (R X = I, X upper triangular): at row i one warp
+// per column c >= i forms the dot product of R's row i with X's column c.
+constexpr int CHOL_SMEM_MAX_K = 112;
+
+__global__ void __launch_bounds__(1024)
+chol_inv_smem_kernel(const double* __restrict__ G, int k, double shift, double* __restrict__ Rout,
+                     double* __restrict__ Rinv, int* status) {
+  extern __shared__ double shm[];
+  double* R = shm;          // k x k
+  double* X = shm + k * k;  // k x k
+  __shared__ int bad;
+  __shared__ double inv_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) bad = 0;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int r = t / k, c = t % k;
+    R[t] = (c >= r) ? G[t] + (r == c ? shift : 0.0) : 0.0;
+    X[t] = 0.0;
+  }
+  __syncthreads();
+  // FP64 square roots and divisions are long instruction sequences on this part: one thread
+  // forms each pivot's reciprocal square root, the others multiply.
+  for (int j = 0; j < k; ++j) {
+    const double d = R[j * k + j];
+    if (!(d > 0.0)) {
+      if (threadIdx.x == 0) bad = 1;
+      break;  // d is read by every thread from shared memory: all leave together
+    }
+    if (threadIdx.x == 0) inv_s = rsqrt(d);
+    __syncthreads();
+    const double inv = inv_s;
+    for (int c = j + threadIdx.x; c < k; c += blockDim.x)
+      R[j * k + c] = (c == j) ? d * inv : R[j * k + c] * inv;
+    __syncthreads();
+    const int rem = k - j - 1;
+    for (int t = threadIdx.x; t < rem * rem; t += blockDim.x) {
+      const int r = j + 1 + t / rem, c = j + 1 + t % rem;
+      if (c >= r) R[r * k + c] -= R[j * k + r] * R[j * k + c];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(status, DEV_CHOL_BREAKDOWN);
+    return;
+  }
+  // Reciprocal diagonal once (R[i][i] holds sqrt(d_i), so 1/R[i][i] = rsqrt(d_i)).
+  for (int i = threadIdx.x; i < k; i += blockDim.x) X[i * k + i] = 1.0 / R[i * k + i];
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    const double rinv = X[i * k + i];
+    for (int c = i + 1 + warp; c < k; c += nw) {
+      double s = 0.0;
+      for (int l = i + 1 + lane; l <= c; l += 32) s = fma(R[i * k + l], X[l * k + c], s);
+      s = warp_sum(s);
+      if (lane == 0) X[i * k + c] = -s * rinv;
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    Rout[t] = R[t];
+    Rinv[t] = X[t];
   }
 }
 
@@ -390,14 +479,9 @@ __global__ void random_cols(double* V, int64_t ld, int n, int c0, int c1, uint64
 }
 
 int cooperative_grid(int work, size_t smem) {
-  static int dev_max = 0;
-  static size_t dev_smem = (size_t)-1;
-  if (dev_smem != smem) {
-    int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_kernel, 256, smem);
-    dev_max = per * num_sms();
-    dev_smem = smem;
-  }
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_kernel, 256, smem);
+  const int dev_max = per * num_sms();
   int want = (work + 255) / 256;
   if (want < 1) want = 1;
   return std::min(want, std::max(dev_max, 1));
@@ -450,12 +534,31 @@ int jacobi_eig(const double* A, int mreal, int64_t lda, double* Qout, double* ev
     TK_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   const int work = h * (h + 1) / 2 + m * h;
-  const int grid = cooperative_grid(std::min(work, 1 << 22), smem);
-  void* args[] = {&g};
   {
     ProfScope prof("jacobi_f64", s, 0.0, 0.0);
     count_launch();
-    TK_CUDA(cudaLaunchCooperativeKernel((void*)jacobi_kernel, grid, 256, args, smem, s));
+    if (m <= CLUSTER_JACOBI_MAX_M) {
+      // One cluster of 8 CTAs x 512 threads: rounds end with the hardware cluster barrier.
+      g.cluster = 1;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(8, 1, 1);
+      cfg.blockDim = dim3(512, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 8;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      TK_CUDA(cudaLaunchKernelEx(&cfg, jacobi_kernel, g));
+    } else {
+      g.cluster = 0;
+      const int grid = cooperative_grid(std::min(work, 1 << 22), smem);
+      void* args[] = {&g};
+      TK_CUDA(cudaLaunchCooperativeKernel((void*)jacobi_kernel, grid, 256, args, smem, s));
+    }
   }
   rank_desc<<<ceil_div(mreal, 256), 256, 0, s>>>(ev.as<double>(), mreal, ord.as<int>());
   TK_LAUNCH();
@@ -485,7 +588,22 @@ int cholqr2(double* V, int64_t ldv, int n, int k, double* T, double* Gk, double*
     bool shifted = false;
     for (int attempt = 0; attempt < 2; ++attempt) {
       TK_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int), s));
-      chol_inv_kernel<<<1, 1024, 0, s>>>(Gk, k, shift, R, Ri, dstat);
+      {
+        ProfScope prof("chol_f64", s, (double)k * k * k, 0.0);
+        if (k <= CHOL_SMEM_MAX_K) {
+          const int smem = 2 * k * k * (int)sizeof(double);
+          static bool attr = false;
+          if (!attr) {
+            TK_CUDA(cudaFuncSetAttribute(chol_inv_smem_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * CHOL_SMEM_MAX_K * CHOL_SMEM_MAX_K * 8));
+            attr = true;
+          }
+          chol_inv_smem_kernel<<<1, 1024, smem, s>>>(Gk, k, shift, R, Ri, dstat);
+        } else {
+          chol_inv_kernel<<<1, 1024, 0, s>>>(Gk, k, shift, R, Ri, dstat);
+        }
+      }
       TK_LAUNCH();
       int h = 0;
       TK_CUDA(cudaMemcpyAsync(&h, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -522,6 +640,7 @@ int deflate(const double* L, int64_t ldl, double* Va, int64_t ldv, int n, int nl
 
 int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, double* lambda,
                  cudaStream_t s, EigStats* st, const float* M32, double tol) {
+  ProfScope prof("eig_topk", s, 0.0, 0.0);
   EigStats local;
   if (!st) st = &local;
   *st = EigStats();

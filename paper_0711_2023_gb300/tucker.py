@@ -60,6 +60,10 @@ _SIGS = {
     "tucker_hooi": (c_int32, [c_void_p, POINTER(c_int32), POINTER(tucker_opts), POINTER(tucker_result)]),
     "tucker_sp": (c_int32, [c_void_p, POINTER(c_int32), POINTER(tucker_opts), POINTER(tucker_result)]),
     "tucker_mp": (c_int32, [c_void_p, POINTER(c_int32), POINTER(tucker_opts), POINTER(tucker_result)]),
+    "tucker_hooi_batched": (c_int32, [c_int32, c_void_p, POINTER(c_int32), POINTER(tucker_opts),
+                                      POINTER(tucker_result)]),
+    "tucker_mp_batched": (c_int32, [c_int32, c_void_p, POINTER(c_int32), POINTER(tucker_opts),
+                                    POINTER(tucker_result)]),
     "tucker_strerror": (c_char_p, [c_int32]),
     "tucker_last_error_detail": (c_char_p, []),
     "tucker_ordering": (c_int32, [c_void_p, c_int32, c_int32, c_int32, POINTER(c_int64), c_void_p,
@@ -269,6 +273,41 @@ def tucker_sp(X: Tensor, J, C_raw, tol=1e-4, max_iter=50, precision="fp64", out=
 
 def tucker_mp(X: Tensor, J, tol=1e-4, max_iter=50, precision="fp64", out="device"):
     return _run("tucker_mp", X, J, precision, tol, max_iter, None, out)
+
+
+def _run_batched(fn_name, Xs, Js, precision, tol, max_iter):
+    torch = _torch()
+    count = len(Xs)
+    o, keep = _opts(precision, tol, max_iter, None)
+    res = (tucker_result * count)()
+    outs = []
+    Jflat = (c_int32 * (3 * count))(*[int(j) for J in Js for j in J])
+    handles = (c_void_p * count)(*[X.handle for X in Xs])
+    for t, (X, J) in enumerate(zip(Xs, Js)):
+        G = torch.empty(tuple(int(j) for j in J), dtype=torch.float64, device="cuda")
+        U = [torch.empty((X.dims[a], int(J[a])), dtype=torch.float64, device="cuda")
+             for a in range(3)]
+        fh = torch.empty(max(1, int(max_iter)), dtype=torch.float64, device="cuda")
+        res[t].G = G.data_ptr()
+        for a in range(3):
+            res[t].U[a] = U[a].data_ptr()
+        res[t].fit_history = fh.data_ptr()
+        res[t].where = TUCKER_DEVICE
+        outs.append((G, U, fh))
+    _check(getattr(_lib(), fn_name)(count, handles, Jflat, ctypes.byref(o), res), fn_name)
+    return [dict(G=G, U=U, fit=float(res[t].fit), iters=int(res[t].iters),
+                 fit_history=fh[:int(res[t].iters)].cpu().numpy().tolist(),
+                 rank_deficient=int(res[t].rank_deficient))
+            for t, (G, U, fh) in enumerate(outs)]
+
+
+def tucker_hooi_batched(Xs, Js, tol=1e-4, max_iter=50, precision="fp64"):
+    """HOOI on a list of tensors (core sizes Js) in one call; a list of per-tensor results."""
+    return _run_batched("tucker_hooi_batched", Xs, Js, precision, tol, max_iter)
+
+
+def tucker_mp_batched(Xs, Js, tol=1e-4, max_iter=50, precision="fp64"):
+    return _run_batched("tucker_mp_batched", Xs, Js, precision, tol, max_iter)
 
 
 # ---- step entry points -------------------------------------------------------------------------
