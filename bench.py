@@ -177,18 +177,24 @@ def timed_region(tk, torch, world, local, steps, make_tensor, C_raw, l2buf, prec
         n, ms, fl, by = tk.tucker_profile_query(name)
         if n:
             prof[name] = {"launches": n, "ms": ms, "flops": fl, "bytes": by}
+    counters = {}
+    for name in COUNTERS:
+        n, _, total, _ = tk.tucker_profile_query(name)
+        counters[name] = {"count": n, "sum": total}
+    prof["counters"] = counters
     tk.tucker_profile_enable(False)
     return total_ms, passes, fits, launches, clk, prof
 
 
 def kernels_only(prof):
-    return {k: v for k, v in prof.items() if k not in STAGES}
+    return {k: v for k, v in prof.items() if k not in STAGES and k != "counters"}
 
 
 KERNELS = ("syrk_f64", "gram_bf16x3", "ttmc_f64", "ttmc_mixed", "slice_proj_f64",
            "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64", "gemm_nn_f32", "gemm_tn_f64",
            "chol_f64", "jacobi_f64", "csf_build")
-STAGES = ("eig_topk",)   # spans that contain many of the kernels above
+STAGES = ("eig_topk", "syev_refined")   # spans that contain many of the kernels above
+COUNTERS = ("eig_outer", "syev_steps", "syev_fallback")   # iteration counts of the eigensolver
 
 
 def roofline_of(prof, name, total_ms, bound, peak, unit, peak_source, per="flops"):
@@ -313,7 +319,9 @@ def profile_leg(args):
     print(json.dumps({"leg": args.profile_leg, "value": passes / (ms / 1e3), "unit": "sweeps/s",
                       "ms_per_step": ms / args.steps, "gpu_launches": launches, "fits": fits,
                       "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                                      "share": round(v["ms"] / ms, 4)} for k, v in prof.items()}}),
+                                      "share": round(v["ms"] / ms, 4)}
+                                  for k, v in prof.items() if k != "counters"},
+                      "eig_counters": prof["counters"]}),
           flush=True)
 
 
@@ -416,7 +424,7 @@ def main():
 
     def kern_table(pr, tot):
         return {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                    "share": round(v["ms"] / tot, 4)} for k, v in pr.items()}
+                    "share": round(v["ms"] / tot, 4)} for k, v in pr.items() if k != "counters"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": world,
@@ -428,12 +436,14 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "fits": fits,
         "kernels": kern_table(prof, total_ms),
+        "eig_counters": prof["counters"],
         "ttmc_f64_gbs": ttmc_gbs,
         "roofline": roofline,
         "mixed": {"value": mx_value, "unit": "sweeps/s", "ms_per_step": mx_ms / args.steps,
                   "speedup_vs_fp64": mx_value / value,
                   "max_abs_dfit_vs_fp64": max(abs(mx_fits[k] - fits[k]) for k in fits),
                   "fits": mx_fits, "kernels": kern_table(mx_prof, mx_ms),
+                  "eig_counters": mx_prof["counters"],
                   "roofline_gram": mx_gram, "gpu_launches": mx_launches, "clocks": mx_clk},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "sweeps/s", "h2d_bytes_per_step": h2d,

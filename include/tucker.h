@@ -200,11 +200,18 @@ int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const dou
 /* ---- profiling (no counterpart in the paper; the paper reports wall time only) ----------
  * tucker_profile_enable(1) clears previous records and starts recording CUDA events on the
  * launching stream around the hot-path kernels; 0 stops.  tucker_profile_query sums, for the
- * kernel `name` ("syrk_f64", "ttmc_f64", "slice_proj_f64", "unfold_gram_f64", "gemm_nn_f64",
- * "jacobi_f64", "csf_build"), the launches recorded, their device time in milliseconds and
- * their algorithmic FLOPs and bytes (what the method must compute and move, not what the
- * kernel happens to do).  tucker_launch_count returns the number of kernels this library has
- * launched in the process. */
+ * record `name`, the launches recorded, their device time in milliseconds and their
+ * algorithmic FLOPs and bytes (what the method must compute and move, not what the kernel
+ * happens to do).  Timed records: the kernels "syrk_f64", "gram_bf16x3", "ttmc_f64",
+ * "ttmc_mixed", "slice_proj_f64", "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64",
+ * "gemm_nn_f32", "gemm_tn_f64", "chol_f64", "jacobi_f64", "csf_build", and the stages
+ * "eig_topk" (one leading-eigenvector solve) and "syev_refined" (one small eigenproblem).
+ * Counters (occurrences as launches, summed values as flops, no time): "syev_steps" (value:
+ * refinement steps of one small eigenproblem), "syev_fallback" (value 1: unresolved cluster,
+ * 2: step limit, 3: order above the shared-memory limit), "eig_outer" (value: Rayleigh-Ritz
+ * iterations of one solve).  Every name and the argument order are fixed; unknown names
+ * report zero.  tucker_launch_count returns the number of kernels this library has launched
+ * in the process. */
 void tucker_profile_enable(int on);
 int tucker_profile_query(const char* name, int64_t* launches, double* total_ms, double* flops,
                          double* bytes);

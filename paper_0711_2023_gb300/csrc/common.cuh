@@ -38,6 +38,9 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 void set_error_detail(const char* msg);
 void keep_pool_memory();  // once per device: freed work buffers stay in the stream pool
 void count_launch();
+// While profiling is enabled, records one occurrence of the counter `name` with `value`
+// (tucker_profile_query reports the occurrences as launches and the sum of values as flops).
+void prof_count(const char* name, double value);
 
 // Records CUDA events around its lifetime on `s` when profiling is enabled
 // (tucker_profile_enable), tagged with the launch's algorithmic FLOPs and bytes.
@@ -64,6 +67,7 @@ enum : int {
   DEV_TIMEOUT = 2,
   DEV_CHOL_BREAKDOWN = 4,
   DEV_NOT_CONVERGED = 8,
+  DEV_CHOL_SHIFTED = 16,
 };
 
 // ---- stream-ordered work buffers ------------------------------------------------------------

@@ -2,12 +2,12 @@
 // "J_n leading eigenvectors of ..." step of every method (Figures HO-SVD3, hooi3, sp3, mp3).
 //
 // Method:
-//   * small n: cyclic two-sided Jacobi on M itself (Golub & Van Loan, Sec. 8.5, parallel
-//     round-robin ordering) in one cooperative launch, FP64;
+//   * small n: all eigenpairs of M at once (syev.cu: FP32 Jacobi refined in FP64, or the FP64
+//     cyclic Jacobi below: Golub & Van Loan, Sec. 8.5, parallel round-robin ordering);
 //   * otherwise block subspace iteration on k = J + max(16, J/2) columns:
 //       - four power steps from the start block (warm start: the previous pass's factor);
-//       - Rayleigh-Ritz (FP64): H = V^T M V, eigenpairs of H by the same Jacobi kernel,
-//         V <- V Q; residuals |M v - theta v| in FP64;
+//       - Rayleigh-Ritz (FP64): H = V^T M V, eigenpairs of H to a tenth of the locking
+//         tolerance (syev.cu), V <- V Q; residuals |M v - theta v| in FP64;
 //       - locking: leading Ritz pairs with residual <= tol * theta_1 are frozen and removed
 //         from the filter's operator, M_d = M - L diag(theta_L) L^T;
 //       - Chebyshev filtering (Zhou & Saad's filtered subspace iteration): p_d(M_d) with the
@@ -15,8 +15,9 @@
 //         block stays well conditioned, two filter applications per Rayleigh-Ritz step (four
 //         power steps while an outlier eigenvalue pins d to 1); optionally the filter's
 //         products run in FP32 until the residuals near the FP32 noise floor;
-//       - Cholesky-QR2 orthonormalisation in FP64 (R = chol(V^T V), V <- V R^-1, twice), with
-//         a shifted pass when the Gram matrix is not numerically positive definite.
+//       - Cholesky-QR2 orthonormalisation in FP64 (R = chol(V^T V), then x R = v solved for
+//         every row v of V, twice), with a shifted pass when the Gram matrix is not
+//         numerically positive definite.
 //   The returned columns are sorted by eigenvalue (largest first) and sign-normalised: the
 //   entry of largest magnitude in each column is positive.
 #include <math.h>
@@ -335,70 +336,148 @@ chol_inv_kernel(const double* __restrict__ G, int k, double shift, double* __res
   }
 }
 
-// The same factorisation with R and R^{-1} in shared memory (k <= CHOL_SMEM_MAX_K).  The
-// inverse is built row by row from the bottom (R X = I, X upper triangular): at row i one warp
-// per column c >= i forms the dot product of R's row i with X's column c.
-constexpr int CHOL_SMEM_MAX_K = 112;
+// Cholesky G + shift I = R^T R without the inverse, for Cholesky-QR by triangular solves.
+// Right-looking, one CTA: step j updates the trailing upper triangle with the unscaled row j,
+// R[r][c] -= R[j][r] R[j][c] / d_j, and rows are scaled by 1/sqrt(d_j) once at the end.  One
+// thread forms each pivot's reciprocal square root (FP64 square roots and divisions are long
+// instruction sequences on this part).  The work array is shared memory for k <= CHOL_SMEM_MAX_K
+// and Rout itself otherwise.  A non-positive pivot restarts the factorisation once with the
+// shift 11 (n k + k (k + 1)) eps tr(G) (shifted Cholesky-QR, Fukaya et al. 2020) and sets
+// DEV_CHOL_SHIFTED; if that fails too, DEV_CHOL_BREAKDOWN.  Outputs: R (k x k, upper, zero
+// below) and rdinv[j] = 1 / R[j][j].
+constexpr int CHOL_SMEM_MAX_K = 160;
+constexpr int TRSM_MAX_K = 384;
 
 __global__ void __launch_bounds__(1024)
-chol_inv_smem_kernel(const double* __restrict__ G, int k, double shift, double* __restrict__ Rout,
-                     double* __restrict__ Rinv, int* status) {
+chol_kernel(const double* __restrict__ G, int k, int64_t nrows, double* __restrict__ Rout,
+            double* __restrict__ rdinv, int* __restrict__ status) {
   extern __shared__ double shm[];
-  double* R = shm;          // k x k
-  double* X = shm + k * k;  // k x k
-  __shared__ int bad;
-  __shared__ double inv_s;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) bad = 0;
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    const int r = t / k, c = t % k;
-    R[t] = (c >= r) ? G[t] + (r == c ? shift : 0.0) : 0.0;
-    X[t] = 0.0;
-  }
-  __syncthreads();
-  // FP64 square roots and divisions are long instruction sequences on this part: one thread
-  // forms each pivot's reciprocal square root, the others multiply.
-  for (int j = 0; j < k; ++j) {
-    const double d = R[j * k + j];
-    if (!(d > 0.0)) {
-      if (threadIdx.x == 0) bad = 1;
-      break;  // d is read by every thread from shared memory: all leave together
-    }
-    if (threadIdx.x == 0) inv_s = rsqrt(d);
-    __syncthreads();
-    const double inv = inv_s;
-    for (int c = j + threadIdx.x; c < k; c += blockDim.x)
-      R[j * k + c] = (c == j) ? d * inv : R[j * k + c] * inv;
-    __syncthreads();
-    const int rem = k - j - 1;
-    for (int t = threadIdx.x; t < rem * rem; t += blockDim.x) {
-      const int r = j + 1 + t / rem, c = j + 1 + t % rem;
-      if (c >= r) R[r * k + c] -= R[j * k + r] * R[j * k + c];
+  __shared__ double dinv_s, shift_s;
+  __shared__ int bad_s;
+  const bool in_smem = k <= CHOL_SMEM_MAX_K;
+  double* R = in_smem ? shm : Rout;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  int attempt = 0;
+  for (; attempt < 2; ++attempt) {
+    if (tid == 0) {
+      bad_s = 0;
+      double sh = 0.0;
+      if (attempt == 1) {
+        double tr = 0.0;
+        for (int i = 0; i < k; ++i) tr += G[(int64_t)i * k + i];
+        sh = 11.0 * ((double)nrows * k + (double)k * (k + 1)) * 2.220446049250313e-16 * tr;
+      }
+      shift_s = sh;
     }
     __syncthreads();
+    const double shift = shift_s;
+    for (int r = warp; r < k; r += nw)
+      for (int c = lane; c < k; c += 32)
+        R[(int64_t)r * k + c] = c >= r ? G[(int64_t)r * k + c] + (c == r ? shift : 0.0) : 0.0;
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+      if (tid == 0) {
+        const double d = R[(int64_t)j * k + j];
+        if (!(d > 0.0)) {
+          bad_s = 1;
+        } else {
+          const double ri = rsqrt(d);
+          rdinv[j] = ri;
+          dinv_s = ri * ri;
+        }
+      }
+      __syncthreads();
+      if (bad_s) break;  // read by all threads after the barrier: uniform
+      const double dinv = dinv_s;
+      const double* Rj = R + (int64_t)j * k;
+      for (int r = j + 1 + warp; r < k; r += nw) {
+        const double f = Rj[r] * dinv;
+        double* Rr = R + (int64_t)r * k;
+        for (int c = r + lane; c < k; c += 32) Rr[c] = fma(-f, Rj[c], Rr[c]);
+      }
+      __syncthreads();
+    }
+    if (!bad_s) break;
+    __syncthreads();
   }
-  __syncthreads();
-  if (bad) {
-    if (threadIdx.x == 0) atomicOr(status, DEV_CHOL_BREAKDOWN);
+  if (attempt == 2) {
+    if (tid == 0) atomicOr(status, DEV_CHOL_BREAKDOWN);
     return;
   }
-  // Reciprocal diagonal once (R[i][i] holds sqrt(d_i), so 1/R[i][i] = rsqrt(d_i)).
-  for (int i = threadIdx.x; i < k; i += blockDim.x) X[i * k + i] = 1.0 / R[i * k + i];
-  __syncthreads();
-  for (int i = k - 1; i >= 0; --i) {
-    const double rinv = X[i * k + i];
-    for (int c = i + 1 + warp; c < k; c += nw) {
-      double s = 0.0;
-      for (int l = i + 1 + lane; l <= c; l += 32) s = fma(R[i * k + l], X[l * k + c], s);
-      s = warp_sum(s);
-      if (lane == 0) X[i * k + c] = -s * rinv;
+  if (attempt == 1 && tid == 0) atomicOr(status, DEV_CHOL_SHIFTED);
+  for (int r = warp; r < k; r += nw) {
+    const double ri = rdinv[r];
+    for (int c = lane; c < k; c += 32)
+      Rout[(int64_t)r * k + c] = c >= r ? R[(int64_t)r * k + c] * ri : 0.0;
+  }
+}
+
+// V <- V R^{-1} in place (x R = v for every row v of V), R upper k x k with rdinv = 1/diag(R).
+// One warp per row; lane l holds entries l, l + 32, ... of the row in registers.  Skipped when
+// the factorisation that made R broke down.
+template <int KT>
+__global__ void __launch_bounds__(256)
+trsm_rows_kernel(double* __restrict__ V, int64_t ldv, int n, int k, const double* __restrict__ R,
+                 const double* __restrict__ rdinv, const int* __restrict__ status) {
+  if (*status & DEV_CHOL_BREAKDOWN) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  double* v = V + row * ldv;
+  double x[KT];
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int l = 32 * t + lane;
+    x[t] = l < k ? v[l] : 0.0;
+  }
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int jend = min(32, k - 32 * t);
+    for (int jj = 0; jj < jend; ++jj) {
+      const int j = 32 * t + jj;
+      const double xj = __shfl_sync(0xffffffffu, x[t], jj) * __ldg(rdinv + j);
+      if (lane == jj) x[t] = xj;
+      const double* Rj = R + (int64_t)j * k;
+#pragma unroll
+      for (int t2 = t; t2 < KT; ++t2) {
+        const int l = 32 * t2 + lane;
+        if (l > j && l < k) x[t2] = fma(-xj, __ldg(Rj + l), x[t2]);
+      }
     }
-    __syncthreads();
   }
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    Rout[t] = R[t];
-    Rinv[t] = X[t];
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int l = 32 * t + lane;
+    if (l < k) v[l] = x[t];
   }
+}
+
+template <int KT>
+void launch_trsm(double* V, int64_t ldv, int n, int k, const double* R, const double* rdinv,
+                 const int* status, cudaStream_t s) {
+  trsm_rows_kernel<KT><<<ceil_div(n, 8), 256, 0, s>>>(V, ldv, n, k, R, rdinv, status);
+}
+
+int trsm_rows(double* V, int64_t ldv, int n, int k, const double* R, const double* rdinv,
+              const int* status, cudaStream_t s) {
+  if (n <= 0) return TUCKER_OK;
+  switch ((k + 31) / 32) {
+    case 1: launch_trsm<1>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 2: launch_trsm<2>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 3: launch_trsm<3>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 4: launch_trsm<4>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 5: launch_trsm<5>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 6: launch_trsm<6>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 7: launch_trsm<7>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 8: launch_trsm<8>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 9: launch_trsm<9>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 10: launch_trsm<10>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 11: launch_trsm<11>(V, ldv, n, k, R, rdinv, status, s); break;
+    case 12: launch_trsm<12>(V, ldv, n, k, R, rdinv, status, s); break;
+    default: return TUCKER_EINVAL;
+  }
+  TK_LAUNCH();
+  return TUCKER_OK;
 }
 
 // r[j] = |W[:, j] - theta[j] V[:, j]|_2, one block per column.
@@ -574,55 +653,108 @@ int jacobi_eig(const double* A, int mreal, int64_t lda, double* Qout, double* ev
   return TUCKER_OK;
 }
 
+int sort_eig_desc(const double* Q, int64_t ldq, int m, const double* ev, double* Qout,
+                  int64_t ldo, double* evals_out, cudaStream_t s) {
+  Buf ord;
+  TK_TRY(ord.alloc(sizeof(int) * m, s));
+  rank_desc<<<ceil_div(m, 256), 256, 0, s>>>(ev, m, ord.as<int>());
+  TK_LAUNCH();
+  permute_cols<<<ceil_div((int64_t)m * m, 256), 256, 0, s>>>(Q, ldq, m, m, ord.as<int>(), Qout,
+                                                             ldo, ev, evals_out);
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
 namespace {
 
-// Cholesky-QR of the n x k block V (ld ldv), in place, until two clean passes (CholQR2).
-// A pass whose Gram matrix is not numerically positive definite is redone with a diagonal
-// shift (shifted Cholesky-QR, Fukaya et al. 2020) and does not count as clean.
-int cholqr2(double* V, int64_t ldv, int n, int k, double* T, double* Gk, double* R, double* Ri,
-            int* dstat, cudaStream_t s) {
-  int clean = 0;
-  for (int pass = 0; pass < 8 && clean < 2; ++pass) {
-    TK_TRY(gemm_tn_f64(k, k, n, V, ldv, V, ldv, Gk, k, s));
-    double shift = 0.0;
-    bool shifted = false;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      TK_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int), s));
-      {
-        ProfScope prof("chol_f64", s, (double)k * k * k, 0.0);
-        if (k <= CHOL_SMEM_MAX_K) {
-          const int smem = 2 * k * k * (int)sizeof(double);
-          static bool attr = false;
-          if (!attr) {
-            TK_CUDA(cudaFuncSetAttribute(chol_inv_smem_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         2 * CHOL_SMEM_MAX_K * CHOL_SMEM_MAX_K * 8));
-            attr = true;
-          }
-          chol_inv_smem_kernel<<<1, 1024, smem, s>>>(Gk, k, shift, R, Ri, dstat);
-        } else {
-          chol_inv_kernel<<<1, 1024, 0, s>>>(Gk, k, shift, R, Ri, dstat);
-        }
-      }
-      TK_LAUNCH();
-      int h = 0;
-      TK_CUDA(cudaMemcpyAsync(&h, dstat, sizeof(int), cudaMemcpyDeviceToHost, s));
-      TK_CUDA(cudaStreamSynchronize(s));
-      if (!(h & DEV_CHOL_BREAKDOWN)) break;
-      if (attempt == 1) return TUCKER_EINTERNAL;
-      // shift = 11 (n k + k (k + 1)) eps |G|_2, with |G|_2 bounded by the trace.
-      std::vector<double> diag(k);
-      TK_CUDA(cudaMemcpy2DAsync(diag.data(), sizeof(double), Gk, sizeof(double) * (k + 1),
-                                sizeof(double), k, cudaMemcpyDeviceToHost, s));
-      TK_CUDA(cudaStreamSynchronize(s));
-      double tr = 0.0;
-      for (double d : diag) tr += d;
-      shift = 11.0 * ((double)n * k + (double)k * (k + 1)) * 2.220446049250313e-16 * tr;
-      shifted = true;
+// Work arrays of cholqr2.
+struct CholWork {
+  double* T;     // n x k (only for k > TRSM_MAX_K)
+  double* Gk;    // k x k
+  double* R;     // k x k
+  double* Ri;    // k x k (only for k > TRSM_MAX_K)
+  double* rd;    // k
+  int* stat;     // 8 status words, one per pass
+};
+
+// One pass for k > TRSM_MAX_K: explicit inverse and a GEMM (the factorisation then runs in
+// global memory on one CTA; such k occur only for very large cores).
+int cholqr_pass_inverse(double* V, int64_t ldv, int n, int k, const CholWork& w, int* stat,
+                        cudaStream_t s, bool* shifted) {
+  TK_TRY(gemm_tn_f64(k, k, n, V, ldv, V, ldv, w.Gk, k, s));
+  double shift = 0.0;
+  *shifted = false;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    TK_CUDA(cudaMemsetAsync(stat, 0, sizeof(int), s));
+    {
+      ProfScope prof("chol_f64", s, (double)k * k * k, 0.0);
+      chol_inv_kernel<<<1, 1024, 0, s>>>(w.Gk, k, shift, w.R, w.Ri, stat);
     }
-    TK_TRY(gemm_nn_f64(n, k, k, 1.0, V, ldv, Ri, k, 0.0, nullptr, 0, 0.0, nullptr, 0, T, k, s));
-    TK_TRY(copy_cols_f64(n, k, T, k, V, ldv, s));
-    if (!shifted) ++clean;
+    TK_LAUNCH();
+    int h = 0;
+    TK_CUDA(cudaMemcpyAsync(&h, stat, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    if (!(h & DEV_CHOL_BREAKDOWN)) break;
+    if (attempt == 1) return TUCKER_EINTERNAL;
+    std::vector<double> diag(k);
+    TK_CUDA(cudaMemcpy2DAsync(diag.data(), sizeof(double), w.Gk, sizeof(double) * (k + 1),
+                              sizeof(double), k, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    double tr = 0.0;
+    for (double d : diag) tr += d;
+    shift = 11.0 * ((double)n * k + (double)k * (k + 1)) * 2.220446049250313e-16 * tr;
+    *shifted = true;
+  }
+  TK_TRY(gemm_nn_f64(n, k, k, 1.0, V, ldv, w.Ri, k, 0.0, nullptr, 0, 0.0, nullptr, 0, w.T, k, s));
+  TK_TRY(copy_cols_f64(n, k, w.T, k, V, ldv, s));
+  return TUCKER_OK;
+}
+
+// One pass for k <= TRSM_MAX_K, all on the device: G = V^T V, R = chol(G) (shifted on
+// breakdown, flagged in *stat), V <- V R^{-1} by row-wise triangular solves.
+int cholqr_pass(double* V, int64_t ldv, int n, int k, const CholWork& w, int* stat,
+                cudaStream_t s) {
+  TK_TRY(gemm_tn_f64(k, k, n, V, ldv, V, ldv, w.Gk, k, s));
+  {
+    ProfScope prof("chol_f64", s, (double)k * k * k / 3.0, 0.0);
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)(sizeof(double) * CHOL_SMEM_MAX_K * CHOL_SMEM_MAX_K));
+    TK_CUDA(attr);
+    const size_t smem = k <= CHOL_SMEM_MAX_K ? sizeof(double) * (size_t)k * k : 0;
+    chol_kernel<<<1, 1024, smem, s>>>(w.Gk, k, n, w.R, w.rd, stat);
+  }
+  TK_LAUNCH();
+  return trsm_rows(V, ldv, n, k, w.R, w.rd, stat, s);
+}
+
+// Cholesky-QR of the n x k block V (ld ldv), in place, until two clean passes (CholQR2).  A
+// pass whose Gram matrix is not numerically positive definite is redone with a diagonal shift
+// and does not count as clean.  Two passes are issued before the one host synchronisation that
+// reads their status words.
+int cholqr2(double* V, int64_t ldv, int n, int k, const CholWork& w, cudaStream_t s) {
+  if (k > TRSM_MAX_K) {
+    int clean = 0;
+    for (int pass = 0; pass < 8 && clean < 2; ++pass) {
+      bool shifted = false;
+      TK_TRY(cholqr_pass_inverse(V, ldv, n, k, w, w.stat, s, &shifted));
+      if (!shifted) ++clean;
+    }
+    return clean >= 2 ? TUCKER_OK : TUCKER_EINTERNAL;
+  }
+  TK_CUDA(cudaMemsetAsync(w.stat, 0, sizeof(int) * 8, s));
+  int issued = 0, clean = 0, checked = 0;
+  int hs[8];
+  while (clean < 2) {
+    const int want = std::min(8, issued + (2 - clean));
+    if (want <= issued) break;
+    for (; issued < want; ++issued) TK_TRY(cholqr_pass(V, ldv, n, k, w, w.stat + issued, s));
+    TK_CUDA(cudaMemcpyAsync(hs, w.stat, sizeof(int) * issued, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    for (; checked < issued; ++checked) {
+      if (hs[checked] & DEV_CHOL_BREAKDOWN) return TUCKER_EINTERNAL;
+      if (!(hs[checked] & DEV_CHOL_SHIFTED)) ++clean;
+    }
   }
   return clean >= 2 ? TUCKER_OK : TUCKER_EINTERNAL;
 }
@@ -648,12 +780,16 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   const int p = std::max(16, J / 2);
   const int k = std::min(n, J + p);
   if (n <= std::max(160, 2 * k)) {
-    // Full Jacobi on M.
+    // All eigenpairs of M at once.
     st->direct = true;
     Buf Qf, ev;
     TK_TRY(Qf.alloc(sizeof(double) * n * n, s));
     TK_TRY(ev.alloc(sizeof(double) * n, s));
-    TK_TRY(jacobi_eig(M, n, n, Qf.as<double>(), ev.as<double>(), s, &st->jacobi_sweeps));
+    SyevStats ss;
+    TK_TRY(syev_refined(M, n, n, Qf.as<double>(), ev.as<double>(), 0.0, 0.1 * tol, s, &ss));
+    st->jacobi_sweeps += ss.fp32_sweeps + ss.fp64_sweeps;
+    st->refine_steps += ss.steps;
+    st->fp64_fallbacks += ss.fallback;
     sign_fix_out<<<J, 256, 0, s>>>(Qf.as<double>(), n, n, U, J);
     TK_LAUNCH();
     std::vector<double> hev(n);
@@ -667,7 +803,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   bool use32 = M32 != nullptr;
   const int max_outer = 120, dmax = 24;
   const double growth_cap = 1e4, abs_cap = 1e8;
-  Buf Vb, T1, T2, T3, H, Qh, evh, Gk, R, Ri, P, rn, stat;
+  Buf Vb, T1, T2, T3, H, Qh, evh, Gk, R, Ri, rd, Tc, P, rn, stat;
   Buf Md, Md32, LS, Lt, lamd;  // deflated filter operator and its factors
   TK_TRY(Md.alloc(sizeof(double) * n * n, s));
   if (M32) TK_TRY(Md32.alloc(sizeof(float) * n * n, s));
@@ -686,10 +822,16 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   TK_TRY(evh.alloc(sizeof(double) * k, s));
   TK_TRY(Gk.alloc(sizeof(double) * k * k, s));
   TK_TRY(R.alloc(sizeof(double) * k * k, s));
-  TK_TRY(Ri.alloc(sizeof(double) * k * k, s));
+  TK_TRY(rd.alloc(sizeof(double) * k, s));
+  if (k > TRSM_MAX_K) {
+    TK_TRY(Ri.alloc(sizeof(double) * k * k, s));
+    TK_TRY(Tc.alloc(nk, s));
+  }
   TK_TRY(P.alloc(sizeof(double) * k * k, s));
   TK_TRY(rn.alloc(sizeof(double) * k, s));
-  TK_TRY(stat.alloc(sizeof(int), s));
+  TK_TRY(stat.alloc(sizeof(int) * 8, s));
+  const CholWork cw{Tc.as<double>(), Gk.as<double>(), R.as<double>(), Ri.as<double>(),
+                    rd.as<double>(), stat.as<int>()};
   double* V = Vb.as<double>();
   int c0 = 0;
   if (U0) {
@@ -699,8 +841,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   random_cols<<<ceil_div((int64_t)n * (k - c0), 256), 256, 0, s>>>(V, k, n, c0, k,
                                                                    0x5EEDull + (uint64_t)n * 131 + J);
   TK_LAUNCH();
-  TK_TRY(cholqr2(V, k, n, k, T1.as<double>(), Gk.as<double>(), R.as<double>(), Ri.as<double>(),
-                 stat.as<int>(), s));
+  TK_TRY(cholqr2(V, k, n, k, cw, s));
   // Power steps before the first Rayleigh-Ritz solve (which on a random or stale block would
   // buy nothing): V <- orth(normalise(M V) + 1e-3 V).  The small multiple of V keeps the block
   // of full rank when M has fewer than k nonzero eigenvalues.
@@ -716,8 +857,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     add_scaled<<<ceil_div((int64_t)n * k, 256), 256, 0, s>>>(W, V, 1e-3, (int64_t)n * k);
     TK_LAUNCH();
     TK_TRY(copy_cols_f64(n, k, W, k, V, k, s));
-    const int qs = cholqr2(V, k, n, k, T2.as<double>(), Gk.as<double>(), R.as<double>(),
-                           Ri.as<double>(), stat.as<int>(), s);
+    const int qs = cholqr2(V, k, n, k, cw, s);
     if (qs != TUCKER_OK) {
       set_error_detail("eigensolver: Cholesky-QR failed in the initial power steps");
       return qs;
@@ -738,9 +878,14 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     TK_TRY(gemm_nn_f64(n, ka, n, 1.0, M, n, Va, k, 0.0, nullptr, 0, 0.0, nullptr, 0, W, ka, s));
     st->matvecs++;
     TK_TRY(gemm_tn_f64(ka, ka, n, Va, k, W, ka, H.as<double>(), ka, s));
-    int sw = 0;
-    const int js = jacobi_eig(H.as<double>(), ka, ka, Qh.as<double>(), evh.as<double>(), s, &sw);
-    st->jacobi_sweeps += sw;
+    // Eigenpairs of H to a tenth of the locking tolerance (relative to the largest Ritz value
+    // seen so far, or to |H| on the first solve).
+    SyevStats ss;
+    const int js = syev_refined(H.as<double>(), ka, ka, Qh.as<double>(), evh.as<double>(),
+                                theta1, 0.1 * tol, s, &ss);
+    st->jacobi_sweeps += ss.fp32_sweeps + ss.fp64_sweeps;
+    st->refine_steps += ss.steps;
+    st->fp64_fallbacks += ss.fallback;
     if (js != TUCKER_OK) return js;
     TK_TRY(gemm_nn_f64(n, ka, ka, 1.0, Va, k, Qh.as<double>(), ka, 0.0, nullptr, 0, 0.0, nullptr,
                        0, T2.as<double>(), ka, s));
@@ -833,8 +978,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
       for (int dd = 0; dd < 2; ++dd) TK_TRY(deflate(V, k, Xa, k, n, nl, ka2, P.as<double>(), s));
       normalize_cols_inplace<<<ka2, 256, 0, s>>>(Xa, k, n);
       TK_LAUNCH();
-      const int qs = cholqr2(Xa, k, n, ka2, T3.as<double>(), Gk.as<double>(), R.as<double>(),
-                             Ri.as<double>(), stat.as<int>(), s);
+      const int qs = cholqr2(Xa, k, n, ka2, cw, s);
       if (qs != TUCKER_OK) {
         char msg[256];
         snprintf(msg, sizeof(msg),
@@ -845,6 +989,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
       }
     }
   }
+  prof_count("eig_outer", (double)st->outer_iters);
   if (!done) {
     char msg[160];
     snprintf(msg, sizeof(msg), "eigensolver: %d outer iterations, %d of %d locked (n=%d)",

@@ -374,12 +374,9 @@ int gram_bf16x3(int rows, int nterms, const GramTerm* terms, double* M, cudaStre
   TK_CUDA(cudaMemcpyAsync(dfirst.p, first.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, s));
   TK_CUDA(cudaMemcpyAsync(dcount.p, count.data(), sizeof(int) * npairs, cudaMemcpyHostToDevice, s));
   TK_CUDA(cudaMemsetAsync(st.p, 0, sizeof(int), s));
-  static bool attr_set = false;
-  if (!attr_set) {
-    TK_CUDA(cudaFuncSetAttribute(gram_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SMEM_BYTES));
-    attr_set = true;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      gram_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  TK_CUDA(attr);
   gram_bf16x3_kernel<<<(unsigned)njobs, 128, SMEM_BYTES, s>>>(maps, djobs.as<Job>(),
                                                                part.as<float>(), st.as<int>());
   TK_LAUNCH();

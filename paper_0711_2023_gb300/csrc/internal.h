@@ -100,10 +100,36 @@ int gram_bf16x3(int rows, int nterms, const GramTerm* terms, double* M, cudaStre
 struct EigStats {
   int outer_iters = 0;
   int matvecs = 0;
-  int jacobi_sweeps = 0;
+  int jacobi_sweeps = 0;     // FP32 pre-solve sweeps plus any FP64 Jacobi sweeps
+  int refine_steps = 0;      // refinement steps of the small eigensolver
+  int fp64_fallbacks = 0;    // small eigenproblems handed to the FP64 Jacobi
   bool direct = false;
   bool rank_deficient = false;
 };
+// Eigen-decomposition of the symmetric m x m matrix A (device, ld lda) by FP64 cyclic Jacobi:
+// Qout (m x m, ld m) gets the eigenvectors as columns in descending eigenvalue order and
+// evals_out (m) the eigenvalues.
+int jacobi_eig(const double* A, int m, int64_t lda, double* Qout, double* evals_out,
+               cudaStream_t s, int* sweeps);
+// Columns of Q (m x m, ld ldq) reordered by descending ev into Qout (ld ldo), ev into evals_out.
+int sort_eig_desc(const double* Q, int64_t ldq, int m, const double* ev, double* Qout,
+                  int64_t ldo, double* evals_out, cudaStream_t s);
+
+// syev.cu: the same contract as jacobi_eig, solved in FP32 and refined in FP64 until every
+// column's off-diagonal mass of X^T A X is below acc_rel * max(|A|_2, scale) and X is
+// orthonormal to 1e-12; falls back to jacobi_eig for m > SYEV_REFINED_MAX_M or when a
+// near-degenerate cluster does not resolve.
+constexpr int SYEV_REFINED_MAX_M = 160;
+struct SyevStats {
+  int steps = 0;
+  int fp32_sweeps = 0;
+  int fp64_sweeps = 0;
+  bool fallback = false;
+  double offdiag = 0.0;  // accepted off-diagonal mass relative to max(|A|_2, scale)
+  double orth = 0.0;
+};
+int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* evals_out,
+                 double scale, double acc_rel, cudaStream_t s, SyevStats* st);
 // Leading J eigenvectors of the symmetric PSD n x n matrix M (device).  U0 (n x J, may be
 // NULL) warm-starts; U (n x J) and lambda (J, may be NULL) receive the result.  Locking
 // residual |M v - theta v| <= tol * theta_1.  With M32 (an FP32 copy of M) the Chebyshev

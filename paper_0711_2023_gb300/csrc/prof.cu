@@ -1,6 +1,6 @@
 // Opt-in kernel timing: CUDA events recorded on the launching stream around the hot-path
-// kernels, with each launch's algorithmic FLOPs and bytes, plus a count of every kernel launch
-// the library makes.  Used by the benchmark to report achieved rates against the roofline.
+// kernels, with each launch's algorithmic FLOPs and bytes, named counters of the iterative
+// parts (values summed), plus a count of every kernel launch the library makes.  Used by the benchmark to report achieved rates against the roofline.
 #include <atomic>
 #include <mutex>
 #include <string.h>
@@ -45,6 +45,12 @@ ProfScope::ProfScope(const char* name, cudaStream_t s, double flops, double byte
   active_ = true;
 }
 
+void prof_count(const char* name, double value) {
+  if (!g_on) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_recs.push_back(Rec{name, nullptr, nullptr, value, 0.0});
+}
+
 ProfScope::~ProfScope() {
   if (!active_) return;
   cudaEventRecord(b_, s_);
@@ -73,6 +79,11 @@ int tucker_profile_query(const char* name, int64_t* launches, double* total_ms, 
   double ms = 0.0, f = 0.0, by = 0.0;
   for (auto& r : g_recs) {
     if (strcmp(r.name, name) != 0) continue;
+    if (!r.a) {  // a counter: no timing, its value summed into *flops
+      ++n;
+      f += r.flops;
+      continue;
+    }
     if (cudaEventSynchronize(r.b) != cudaSuccess) return TUCKER_ECUDA;
     float t = 0.f;
     if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return TUCKER_ECUDA;

@@ -1,0 +1,357 @@
+// Small dense symmetric eigenproblems (order m <= SYEV_REFINED_MAX_M): the Rayleigh-Ritz
+// matrix H = V^T M V of the subspace iteration and, for small unfoldings, M itself.
+//
+// FP64 arithmetic is a narrow pipe on this part (about 2 FMA per clock per SM), so a cyclic
+// Jacobi in FP64 is bound by the latency of its m - 1 rounds per sweep.  Instead:
+//   1. a cyclic round-robin Jacobi in FP32, all of it in one CTA's shared memory, gives an
+//      approximate eigenvector matrix X (accurate to ~1e-7 of |A|);
+//   2. Ogita & Aishima's iterative refinement for the symmetric eigenproblem (Japan J. Indust.
+//      Appl. Math. 35, 2018) brings X to FP64 accuracy.  One step, all in FP64:
+//          R = I - X^T X,  S = X^T A X,  lambda_i = s_ii / (1 - r_ii),
+//          E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)   (i != j, separated pair),
+//          E_ij = r_ij / 2                                          (i == j, or unresolved),
+//          X <- X + X E.
+//      A pair counts as separated when its first-order correction is small against its gap,
+//      |s_ij + lambda_j r_ij| <= 0.1 |lambda_j - lambda_i|, and the gap is above the FP64 noise
+//      floor; the products are FP64 GEMMs spread over the whole GPU.  Convergence is quadratic.
+//   3. The result is accepted once every column's off-diagonal mass |S_{:,j}|_offdiag is below
+//      the caller's threshold and the loss of orthogonality max |R| is below 1e-12.  S and G
+//      are symmetrised before use (see oa_column_kernel).  A near-degenerate
+//      cluster that the first-order step cannot split (and that would matter at the caller's
+//      tolerance) sends the problem to the FP64 Jacobi instead.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace tk {
+
+namespace {
+
+constexpr int JAC32_MAX_H = SYEV_REFINED_MAX_M / 2;
+
+__device__ __forceinline__ int rr_slot(int j, int r, int m) {
+  return j == 0 ? 0 : 1 + (j - 1 + r) % (m - 1);
+}
+
+// Cyclic Jacobi on FP32(0.5 (A + A^T)) in shared memory (scaled by a power of two when its
+// entries lie outside FP32's comfortable range), round-robin ordering: round r rotates the m/2
+// disjoint pairs at once.  A rotation is applied when |a_pq| exceeds both tol_abs * max |a_ii|
+// and tol_rel * sqrt|a_pp a_qq|; the sweep loop ends after a sweep without one.  The
+// update is in place: block (I, K) of J^T A J reads and writes only rows {p_I, q_I} x columns
+// {p_K, q_K}, which no other block touches.  Q is kept transposed so that the rows of a pair's
+// two columns are contiguous for the lanes.  X (m x m, FP64, ld ldx) receives Q.
+__global__ void __launch_bounds__(1024)
+jacobi32_kernel(const double* __restrict__ A, int m, int64_t lda, float tol_rel, float tol_abs,
+                int max_sweeps, double* __restrict__ X, int64_t ldx, int* __restrict__ info) {
+  extern __shared__ float smf[];
+  const int mp = m + (m & 1), h = mp / 2;
+  float* a = smf;             // mp x mp
+  float* qt = a + mp * mp;    // qt[c * mp + r] = Q[r][c]
+  __shared__ float cs[JAC32_MAX_H], sn[JAC32_MAX_H], dp[JAC32_MAX_H], dq[JAC32_MAX_H];
+  __shared__ int pi[JAC32_MAX_H], qi[JAC32_MAX_H], on_s[JAC32_MAX_H];
+  __shared__ float dmax_s;
+  __shared__ unsigned long long amax_s;
+  __shared__ double pow2_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // max |a_ij| from the bit patterns (integer compares keep this off the FP64 pipe)
+  if (tid == 0) amax_s = 0ull;
+  __syncthreads();
+  unsigned long long mb = 0ull;
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int r = t / m, c = t - r * m;
+    const unsigned long long b =
+        (unsigned long long)__double_as_longlong(A[(int64_t)r * lda + c]) & 0x7fffffffffffffffull;
+    mb = b > mb ? b : mb;
+  }
+  atomicMax(&amax_s, mb);
+  __syncthreads();
+  if (tid == 0) {
+    // A power of two that brings max |a_ij| near 1 when FP32 could not hold it as it is.
+    const double amax = __longlong_as_double((long long)amax_s);
+    int e = 0;
+    if (amax > 0.0) frexp(amax, &e);
+    pow2_s = (amax > 1e30 || (amax > 0.0 && amax < 1e-30)) ? ldexp(1.0, -e) : 1.0;
+  }
+  __syncthreads();
+  const double pw = pow2_s;
+  for (int t = tid; t < mp * mp; t += blockDim.x) {
+    const int r = t / mp, c = t - r * mp;
+    float v = 0.0f;
+    if (r < m && c < m) {
+      double x = A[(int64_t)r * lda + c], y = A[(int64_t)c * lda + r];
+      if (pw != 1.0) { x *= pw; y *= pw; }
+      v = 0.5f * ((float)x + (float)y);
+    }
+    a[t] = v;
+    qt[t] = (r == c) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float mx = 0.0f;
+    for (int i = lane; i < m; i += 32) mx = fmaxf(mx, fabsf(a[i * mp + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) dmax_s = mx;
+  }
+  __syncthreads();
+  const float abs_thr = tol_abs * dmax_s;
+  int sweep = 0, converged = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    int active_sweep = 0;
+    for (int r = 0; r < mp - 1; ++r) {
+      int on = 0;
+      if (tid < h) {
+        const int x = rr_slot(tid, r, mp), y = rr_slot(mp - 1 - tid, r, mp);
+        const int p = min(x, y), q = max(x, y);
+        const float app = a[p * mp + p], aqq = a[q * mp + q], apq = a[p * mp + q];
+        float c = 1.0f, s = 0.0f, np_ = app, nq_ = aqq;
+        if (fabsf(apq) > abs_thr && fabsf(apq) > tol_rel * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
+          // Symmetric 2x2 Schur decomposition (Golub & Van Loan, Algorithm 8.4.1).
+          const float tau = (aqq - app) / (2.0f * apq);
+          const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+          c = rsqrtf(fmaf(t, t, 1.0f));
+          s = t * c;
+          np_ = app - t * apq;
+          nq_ = aqq + t * apq;
+          on = 1;
+        }
+        cs[tid] = c; sn[tid] = s; dp[tid] = np_; dq[tid] = nq_;
+        pi[tid] = p; qi[tid] = q; on_s[tid] = on;
+      }
+      if (!__syncthreads_or(on)) continue;  // nothing to rotate this round (uniform)
+      active_sweep = 1;
+      for (int I = warp; I < h; I += nw) {
+        const float c1 = cs[I], s1 = sn[I];
+        const int p = pi[I], q = qi[I];
+        for (int K = lane; K < h; K += 32) {
+          if (K == I) {
+            if (on_s[I]) {
+              a[p * mp + p] = dp[I];
+              a[q * mp + q] = dq[I];
+              a[p * mp + q] = 0.0f;
+              a[q * mp + p] = 0.0f;
+            }
+            continue;
+          }
+          const float c2 = cs[K], s2 = sn[K];
+          if (s1 == 0.0f && s2 == 0.0f) continue;
+          const int u = pi[K], v = qi[K];
+          const float x0 = a[p * mp + u], x1 = a[p * mp + v];
+          const float x2 = a[q * mp + u], x3 = a[q * mp + v];
+          const float rpu = c1 * x0 - s1 * x2, rpv = c1 * x1 - s1 * x3;
+          const float rqu = s1 * x0 + c1 * x2, rqv = s1 * x1 + c1 * x3;
+          a[p * mp + u] = c2 * rpu - s2 * rpv;
+          a[p * mp + v] = s2 * rpu + c2 * rpv;
+          a[q * mp + u] = c2 * rqu - s2 * rqv;
+          a[q * mp + v] = s2 * rqu + c2 * rqv;
+        }
+        if (s1 != 0.0f) {
+          // Q <- Q J: columns p and q of Q are rows p and q of qt.
+          for (int row = lane; row < mp; row += 32) {
+            const float y0 = qt[p * mp + row], y1 = qt[q * mp + row];
+            qt[p * mp + row] = c1 * y0 - s1 * y1;
+            qt[q * mp + row] = s1 * y0 + c1 * y1;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!active_sweep) {
+      converged = 1;
+      ++sweep;
+      break;
+    }
+  }
+  for (int t = tid; t < m * m; t += blockDim.x) {
+    const int r = t / m, c = t - r * m;
+    X[(int64_t)r * ldx + c] = (double)qt[c * mp + r];
+  }
+  if (tid == 0) {
+    info[0] = sweep;
+    info[1] = converged;
+  }
+}
+
+// lambda_i = s_ii / g_ii (g = X^T X, so 1 - r_ii = g_ii), one thread per i.
+__global__ void oa_lambda_kernel(const double* __restrict__ SG, int m, int64_t ld,
+                                 double* __restrict__ lam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) lam[i] = SG[(int64_t)i * ld + i] / SG[(int64_t)i * ld + m + i];
+}
+
+// One block per column j of the refinement: E[:, j], and the column's statistics
+//   stats[3j]     = sum_{i != j} s_ij^2,
+//   stats[3j + 1] = max_i |r_ij|,
+//   stats[3j + 2] = pairs (i, j) left unresolved with |s_ij| > bad_thr_rel * max(nA, scale).
+// nA = max_i |lambda_i| is recomputed by every block (m values).
+__global__ void __launch_bounds__(256)
+oa_column_kernel(const double* __restrict__ SG, int m, int64_t ld, const double* __restrict__ lam,
+                 double scale, double bad_thr_rel, double* __restrict__ E,
+                 double* __restrict__ stats) {
+  __shared__ double red[3][8];
+  __shared__ double nA_s;
+  const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double mx = 0.0;
+  for (int i = tid; i < m; i += blockDim.x) mx = fmax(mx, fabs(lam[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[0][warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[0][w]);
+    nA_s = t;
+  }
+  __syncthreads();
+  const double nA = nA_s;
+  const double lj = lam[j];
+  const double floor_gap = 1e-13 * nA;
+  const double bad_thr = bad_thr_rel * fmax(nA, scale);
+  double off2 = 0.0, orth = 0.0, bad = 0.0;
+  for (int i = tid; i < m; i += blockDim.x) {
+    // S and G are symmetric in exact arithmetic; their rounded products are not, and an
+    // asymmetry divided by a small gap would leave an orthogonality floor far above eps.
+    const double s = 0.5 * (SG[(int64_t)i * ld + j] + SG[(int64_t)j * ld + i]);
+    const double g = 0.5 * (SG[(int64_t)i * ld + m + j] + SG[(int64_t)j * ld + m + i]);
+    const double r = (i == j ? 1.0 : 0.0) - g;
+    orth = fmax(orth, fabs(r));
+    double e = 0.5 * r;
+    if (i != j) {
+      off2 = fma(s, s, off2);
+      const double num = fma(lj, r, s), den = lj - lam[i];
+      if (fabs(den) > floor_gap && fabs(num) <= 0.1 * fabs(den)) {
+        e = num / den;
+      } else if (fabs(s) > bad_thr) {
+        bad += 1.0;
+      }
+    }
+    E[(int64_t)i * m + j] = e;
+  }
+  off2 = warp_sum(off2);
+  bad = warp_sum(bad);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) orth = fmax(orth, __shfl_xor_sync(0xffffffffu, orth, o));
+  __syncthreads();
+  if (lane == 0) {
+    red[0][warp] = off2;
+    red[1][warp] = orth;
+    red[2][warp] = bad;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b = fmax(b, red[1][w]);
+      c += red[2][w];
+    }
+    stats[3 * j] = a;
+    stats[3 * j + 1] = b;
+    stats[3 * j + 2] = c;
+  }
+}
+
+}  // namespace
+
+int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* evals_out,
+                 double scale, double acc_rel, cudaStream_t s, SyevStats* st) {
+  SyevStats local;
+  if (!st) st = &local;
+  *st = SyevStats();
+  if (m <= 0) return TUCKER_EINVAL;
+  if (m > SYEV_REFINED_MAX_M) {
+    st->fallback = true;
+    prof_count("syev_fallback", 3.0);
+    return jacobi_eig(A, m, lda, Qout, evals_out, s, &st->fp64_sweeps);
+  }
+  ProfScope prof("syev_refined", s, 0.0, 0.0);
+  const int mp = m + (m & 1);
+  const int64_t ld = 2 * (int64_t)m;  // [W | X] and [S | G] side by side
+  Buf WX0, WX1, SG, E, lam, stats, info;
+  TK_TRY(WX0.alloc(sizeof(double) * m * ld, s));
+  TK_TRY(WX1.alloc(sizeof(double) * m * ld, s));
+  TK_TRY(SG.alloc(sizeof(double) * m * ld, s));
+  TK_TRY(E.alloc(sizeof(double) * m * m, s));
+  TK_TRY(lam.alloc(sizeof(double) * m, s));
+  TK_TRY(stats.alloc(sizeof(double) * 3 * m, s));
+  TK_TRY(info.alloc(sizeof(int) * 2, s));
+  double* cur = WX0.as<double>();
+  double* nxt = WX1.as<double>();
+  {
+    const size_t smem = 2 * sizeof(float) * (size_t)mp * mp;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)(2 * sizeof(float) * SYEV_REFINED_MAX_M * SYEV_REFINED_MAX_M));
+    TK_CUDA(attr);
+    jacobi32_kernel<<<1, 1024, smem, s>>>(A, m, lda, 1e-6f, 1e-7f, 40, cur + m, ld,
+                                          info.as<int>());
+    TK_LAUNCH();
+  }
+  // Refinement.  The statistics are read back (one host synchronisation each) from the step
+  // `first_check` on: from an FP32 start the first two steps never meet the orthogonality bar.
+  const int max_steps = 6;
+  const int first_check = 2;
+  const double bad_rel = acc_rel;
+  std::vector<double> hs(3 * (size_t)m);
+  bool accepted = false, cluster = false;
+  int step = 0;
+  for (; step <= max_steps; ++step) {
+    double* X = cur + m;
+    TK_TRY(gemm_nn_f64(m, m, m, 1.0, A, lda, X, ld, 0.0, nullptr, 0, 0.0, nullptr, 0, cur, ld, s));
+    TK_TRY(gemm_tn_f64(m, 2 * m, m, X, ld, cur, ld, SG.as<double>(), ld, s));
+    oa_lambda_kernel<<<ceil_div(m, 128), 128, 0, s>>>(SG.as<double>(), m, ld, lam.as<double>());
+    TK_LAUNCH();
+    oa_column_kernel<<<m, 256, 0, s>>>(SG.as<double>(), m, ld, lam.as<double>(), scale, bad_rel,
+                                       E.as<double>(), stats.as<double>());
+    TK_LAUNCH();
+    if (step >= first_check) {
+      TK_CUDA(cudaMemcpyAsync(hs.data(), stats.p, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost,
+                              s));
+      double hl_max = 0.0;
+      std::vector<double> hl(m);
+      TK_CUDA(cudaMemcpyAsync(hl.data(), lam.p, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaStreamSynchronize(s));
+      for (double v : hl) hl_max = std::max(hl_max, fabs(v));
+      const double thr = acc_rel * std::max(hl_max, scale);
+      double off = 0.0, orth = 0.0, bad = 0.0;
+      for (int j = 0; j < m; ++j) {
+        off = std::max(off, sqrt(hs[3 * j]));
+        orth = std::max(orth, hs[3 * j + 1]);
+        bad += hs[3 * j + 2];
+      }
+      st->offdiag = off / std::max(std::max(hl_max, scale), 1e-300);
+      st->orth = orth;
+      if (off <= thr && orth <= 1e-12) {
+        accepted = true;
+        break;
+      }
+      // An unresolved cluster that matters does not get better by more first-order steps.
+      if (bad > 0.0 && step >= first_check + 1) {
+        cluster = true;
+        break;
+      }
+    }
+    if (step == max_steps) break;
+    // X <- X + X E into the other buffer.
+    TK_TRY(gemm_nn_f64(m, m, m, 1.0, X, ld, E.as<double>(), m, 1.0, X, ld, 0.0, nullptr, 0,
+                       nxt + m, ld, s));
+    std::swap(cur, nxt);
+  }
+  st->steps = step;
+  int hinfo[2] = {0, 0};
+  TK_CUDA(cudaMemcpyAsync(hinfo, info.p, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  st->fp32_sweeps = hinfo[0];
+  prof_count("syev_steps", (double)step);
+  if (!accepted) {
+    st->fallback = true;
+    prof_count("syev_fallback", cluster ? 1.0 : 2.0);
+    return jacobi_eig(A, m, lda, Qout, evals_out, s, &st->fp64_sweeps);
+  }
+  return sort_eig_desc(cur + m, ld, m, lam.as<double>(), Qout, m, evals_out, s);
+}
+
+}  // namespace tk
