@@ -193,8 +193,8 @@ def kernels_only(prof):
 KERNELS = ("syrk_f64", "gram_bf16x3", "ttmc_f64", "ttmc_mixed", "slice_proj_f64",
            "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64", "gemm_nn_f32", "gemm_tn_f64",
            "chol_f64", "jacobi_f64", "csf_build")
-STAGES = ("eig_topk", "syev_refined")   # spans that contain many of the kernels above
-COUNTERS = ("eig_outer", "syev_steps", "syev_fallback")   # iteration counts of the eigensolver
+STAGES = ("eig_topk", "syev_refined", "syev_jacobi32")   # spans that contain many of the kernels above
+COUNTERS = ("eig_outer", "syev_steps", "syev_fp32_sweeps", "syev_fallback")   # iteration counts of the eigensolver
 
 
 def roofline_of(prof, name, total_ms, bound, peak, unit, peak_source, per="flops"):
@@ -290,10 +290,22 @@ def batched_leg(args):
     b.synchronize()
     wall = time.perf_counter() - t0
     passes = args.steps * len(Ts) * 2 * SWEEPS
+    # The plain FP64 path on the same tensors, one call at a time (a bounded sample: the first
+    # 32 tensors), for the comparison in the same units.
+    ns = min(32, len(Ts))
+    t0 = time.perf_counter()
+    for t in range(ns):
+        tk.tucker_hooi(Ts[t], Js[t], tol=-np.inf, max_iter=SWEEPS, precision="fp64")
+        tk.tucker_mp(Ts[t], Js[t], tol=-np.inf, max_iter=SWEEPS, precision="fp64")
+    torch.cuda.synchronize()
+    single = time.perf_counter() - t0
     print(json.dumps({"leg": "batched", "tensors": len(Ts), "nnz_total": nnz_total,
                       "value": passes / wall, "unit": "tensor-sweeps/s",
                       "ms_per_step": 1e3 * wall / args.steps, "steps": args.steps,
                       "warmup": args.warmup, "precision": "mixed",
+                      "fp64_one_at_a_time": {"value": ns * 2 * SWEEPS / single,
+                                             "unit": "tensor-sweeps/s",
+                                             "sample": f"first {ns} tensors, HOOI + MP"},
                       "note": "wall clock around the batched calls (they synchronise)"}),
           flush=True)
 

@@ -205,9 +205,11 @@ int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const dou
  * happens to do).  Timed records: the kernels "syrk_f64", "gram_bf16x3", "ttmc_f64",
  * "ttmc_mixed", "slice_proj_f64", "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64",
  * "gemm_nn_f32", "gemm_tn_f64", "chol_f64", "jacobi_f64", "csf_build", and the stages
- * "eig_topk" (one leading-eigenvector solve) and "syev_refined" (one small eigenproblem).
+ * "eig_topk" (one leading-eigenvector solve) and "syev_refined" (one small eigenproblem) with
+ * "syev_jacobi32" (its FP32 Jacobi).
  * Counters (occurrences as launches, summed values as flops, no time): "syev_steps" (value:
- * refinement steps of one small eigenproblem), "syev_fallback" (value 1: unresolved cluster,
+ * refinement steps of one small eigenproblem), "syev_fp32_sweeps" (value: sweeps of its FP32
+ * Jacobi), "syev_fallback" (value 1: unresolved cluster,
  * 2: step limit, 3: order above the shared-memory limit), "eig_outer" (value: Rayleigh-Ritz
  * iterations of one solve).  Every name and the argument order are fixed; unknown names
  * report zero.  tucker_launch_count returns the number of kernels this library has launched

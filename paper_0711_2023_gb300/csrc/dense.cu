@@ -86,52 +86,55 @@ gemm_nn_kernel(int m, int n, int k, double alpha, const TA* __restrict__ A, int6
   }
 }
 
-// Partial P[split] = A[k-range]^T B[k-range], 64 x 64 output tile per CTA.
+// FP64 C = alpha * op(A) B + beta * X + gamma * Z with op(A) = A^T when TA (A: k x m) and A
+// otherwise (A: m x k); a 16 x 16 output tile per CTA, one output per thread.  FP64 FMA
+// throughput (about 2 per clock per SM on this part) bounds every FP64 product of the
+// eigensolver, so the tile is sized to fill all SMs with little padding (75 columns pad to 80,
+// not 128), not for register reuse.  With P given the CTA writes its raw partial over K-slice
+// blockIdx.z to P[blockIdx.z] and reduce_nn applies the epilogue.
+template <bool TA>
 __global__ void __launch_bounds__(256)
-gemm_tn_kernel(int m, int n, int64_t k, int64_t kchunk, const double* __restrict__ A,
-               int64_t lda, const double* __restrict__ B, int64_t ldb, double* __restrict__ P) {
-  __shared__ double As[BK][BM];
-  __shared__ double Bs[BK][BN];
+gemm16_kernel(int m, int n, int64_t k, double alpha, const double* __restrict__ A, int64_t lda,
+              const double* __restrict__ B, int64_t ldb, double beta, const double* Xm,
+              int64_t ldx, double gamma, const double* __restrict__ Zm, int64_t ldz, double* C,
+              int64_t ldc, int64_t kchunk, double* __restrict__ P) {
+  __shared__ double As[16][17];  // [i][kk]
+  __shared__ double Bs[16][17];  // [kk][j]
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m0 = blockIdx.y * 16, n0 = blockIdx.x * 16;
   const int64_t kb = (int64_t)blockIdx.z * kchunk;
   const int64_t ke = min64(k, kb + kchunk);
-  double acc[4][4] = {};
-  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int idx = threadIdx.x + 256 * e;
-      const int r = idx / BM, c = idx % BM;  // 16 rows (k) x 64 cols
-      const int64_t kr = k0 + r;
-      As[r][c] = (kr < ke && m0 + c < m) ? A[kr * lda + m0 + c] : 0.0;
-      Bs[r][c] = (kr < ke && n0 + c < n) ? B[kr * ldb + n0 + c] : 0.0;
+  double acc = 0.0;
+  for (int64_t k0 = kb; k0 < ke; k0 += 16) {
+    if (TA) {
+      const int64_t kr = k0 + ty;
+      const int gi = m0 + tx;
+      As[tx][ty] = (kr < ke && gi < m) ? A[kr * lda + gi] : 0.0;
+    } else {
+      const int gi = m0 + ty;
+      const int64_t kc = k0 + tx;
+      As[ty][tx] = (gi < m && kc < ke) ? A[(int64_t)gi * lda + kc] : 0.0;
+    }
+    {
+      const int64_t kr = k0 + ty;
+      const int gj = n0 + tx;
+      Bs[ty][tx] = (kr < ke && gj < n) ? B[kr * ldb + gj] : 0.0;
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
+    for (int kk = 0; kk < 16; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
     __syncthreads();
   }
-  double* Pz = P + (int64_t)blockIdx.z * m * n;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = m0 + ty + 16 * i;
-    if (r >= m) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = n0 + tx + 16 * j;
-      if (c < n) Pz[(int64_t)r * n + c] = acc[i][j];
-    }
+  const int r = m0 + ty, c = n0 + tx;
+  if (r >= m || c >= n) return;
+  if (P) {
+    P[(int64_t)blockIdx.z * m * n + (int64_t)r * n + c] = acc;
+    return;
   }
+  double v = alpha * acc;
+  if (Xm) v = fma(beta, Xm[(int64_t)r * ldx + c], v);
+  if (Zm) v = fma(gamma, Zm[(int64_t)r * ldz + c], v);
+  C[(int64_t)r * ldc + c] = v;
 }
 
 // C = alpha * (sum of the split partials, in split order) + beta * X + gamma * Z.
@@ -147,15 +150,6 @@ __global__ void reduce_nn(const double* __restrict__ P, int splits, int m, int n
   if (Xm) v = fma(beta, Xm[r * ldx + c], v);
   if (Zm) v = fma(gamma, Zm[r * ldz + c], v);
   C[r * ldc + c] = v;
-}
-
-__global__ void reduce_splits(const double* __restrict__ P, int splits, int m, int n,
-                              double* __restrict__ C, int64_t ldc) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)m * n) return;
-  double s = 0.0;
-  for (int z = 0; z < splits; ++z) s += P[(int64_t)z * m * n + t];
-  C[(t / n) * ldc + (t % n)] = s;
 }
 
 // SYRK partials over lower-triangle tile pairs (ti >= tj) of rows x rows; K is the
@@ -299,13 +293,48 @@ int gemm_nn_impl(const char* name, int m, int n, int k, double alpha, const TA* 
   return TUCKER_OK;
 }
 
+template <bool TA>
+int gemm16(const char* name, int m, int n, int64_t k, double alpha, const double* A, int64_t lda,
+           const double* B, int64_t ldb, double beta, const double* Xm, int64_t ldx, double gamma,
+           const double* Zm, int64_t ldz, double* C, int64_t ldc, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return TUCKER_OK;
+  ProfScope prof(name, s, 2.0 * m * n * (double)k,
+                 8.0 * ((double)m * k + (double)k * n + (double)m * n));
+  const int tiles = ceil_div(n, 16) * ceil_div(m, 16);
+  // Enough CTAs for two per SM; K slices of at least 64, summed in a fixed order.
+  int64_t splits = 1;
+  const int want = 2 * num_sms();
+  if (tiles < want && k >= 128) splits = std::min<int64_t>((want + tiles - 1) / tiles, k / 64);
+  int64_t kchunk = (k + splits - 1) / splits;
+  kchunk = std::max<int64_t>(16, (kchunk + 15) / 16 * 16);
+  splits = (k + kchunk - 1) / kchunk;
+  if (splits <= 1) {
+    dim3 grid(ceil_div(n, 16), ceil_div(m, 16), 1);
+    gemm16_kernel<TA><<<grid, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, Xm, ldx, gamma,
+                                           Zm, ldz, C, ldc, std::max<int64_t>(k, 1), nullptr);
+    TK_LAUNCH();
+    return TUCKER_OK;
+  }
+  Buf P;
+  TK_TRY(P.alloc(sizeof(double) * (size_t)splits * m * n, s));
+  dim3 grid(ceil_div(n, 16), ceil_div(m, 16), (unsigned)splits);
+  gemm16_kernel<TA><<<grid, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, Xm, ldx, gamma,
+                                         Zm, ldz, C, ldc, kchunk, P.as<double>());
+  TK_LAUNCH();
+  reduce_nn<<<ceil_div((int64_t)m * n, 256), 256, 0, s>>>(P.as<double>(), (int)splits, m, n,
+                                                          alpha, beta, Xm, ldx, gamma, Zm, ldz,
+                                                          C, ldc);
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
 }  // namespace
 
 int gemm_nn_f64(int m, int n, int k, double alpha, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double beta, const double* Xm, int64_t ldx, double gamma,
                 const double* Zm, int64_t ldz, double* C, int64_t ldc, cudaStream_t s) {
-  return gemm_nn_impl<double, double>("gemm_nn_f64", m, n, k, alpha, A, lda, B, ldb, beta, Xm,
-                                      ldx, gamma, Zm, ldz, C, ldc, s);
+  return gemm16<false>("gemm_nn_f64", m, n, k, alpha, A, lda, B, ldb, beta, Xm, ldx, gamma, Zm,
+                       ldz, C, ldc, s);
 }
 
 int gemm_nn_f32a(int m, int n, int k, double alpha, const float* A, int64_t lda, const double* B,
@@ -317,24 +346,8 @@ int gemm_nn_f32a(int m, int n, int k, double alpha, const float* A, int64_t lda,
 
 int gemm_tn_f64(int m, int n, int64_t k, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
-  if (m <= 0 || n <= 0) return TUCKER_OK;
-  ProfScope prof("gemm_tn_f64", s, 2.0 * m * n * (double)k,
-                 8.0 * ((double)m * k + (double)k * n + (double)m * n));
-  const int tiles = ceil_div(m, BM) * ceil_div(n, BN);
-  const int splits = choose_splits(tiles, k);
-  int64_t kchunk = (k + splits - 1) / splits;
-  kchunk = (kchunk + BK - 1) / BK * BK;
-  if (kchunk == 0) kchunk = BK;
-  const int nsplit = (int)((k + kchunk - 1) / kchunk > 0 ? (k + kchunk - 1) / kchunk : 1);
-  Buf P;
-  TK_TRY(P.alloc(sizeof(double) * (size_t)nsplit * m * n, s));
-  dim3 grid(ceil_div(n, BN), ceil_div(m, BM), nsplit);
-  gemm_tn_kernel<<<grid, 256, 0, s>>>(m, n, k, kchunk, A, lda, B, ldb, P.as<double>());
-  TK_LAUNCH();
-  reduce_splits<<<ceil_div((int64_t)m * n, 256), 256, 0, s>>>(P.as<double>(), nsplit, m, n, C,
-                                                               ldc);
-  TK_LAUNCH();
-  return TUCKER_OK;
+  return gemm16<true>("gemm_tn_f64", m, n, k, 1.0, A, lda, B, ldb, 0.0, nullptr, 0, 0.0, nullptr,
+                      0, C, ldc, s);
 }
 
 int syrk_f64(int rows, const double* Y1, int64_t K1, const double* Y2, int64_t K2, double* M,

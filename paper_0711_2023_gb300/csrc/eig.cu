@@ -337,7 +337,8 @@ chol_inv_kernel(const double* __restrict__ G, int k, double shift, double* __res
 }
 
 // Cholesky G + shift I = R^T R without the inverse, for Cholesky-QR by triangular solves.
-// Right-looking, one CTA: step j updates the trailing upper triangle with the unscaled row j,
+// A G within 2^-27 of the identity takes the first-order factor (below).  Otherwise
+// right-looking, one CTA: step j updates the trailing upper triangle with the unscaled row j,
 // R[r][c] -= R[j][r] R[j][c] / d_j, and rows are scaled by 1/sqrt(d_j) once at the end.  One
 // thread forms each pivot's reciprocal square root (FP64 square roots and divisions are long
 // instruction sequences on this part).  The work array is shared memory for k <= CHOL_SMEM_MAX_K
@@ -357,6 +358,33 @@ chol_kernel(const double* __restrict__ G, int k, int64_t nrows, double* __restri
   const bool in_smem = k <= CHOL_SMEM_MAX_K;
   double* R = in_smem ? shm : Rout;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // Near-identity fast path (the second pass of Cholesky-QR): for G = I + F with max |F| below
+  // 2^-27, R = I + triu(F, 1) + diag(F) / 2 is exact to O(|F|^2) < eps, with no serial
+  // factorisation.  max |F| is taken over the bit patterns (no FP64 compares).
+  {
+    __shared__ unsigned long long fmax_s;
+    if (tid == 0) fmax_s = 0ull;
+    __syncthreads();
+    unsigned long long mb = 0ull;
+    for (int r = warp; r < k; r += nw)
+      for (int c = r + lane; c < k; c += 32) {
+        const double f = G[(int64_t)r * k + c] - (c == r ? 1.0 : 0.0);
+        const unsigned long long b =
+            (unsigned long long)__double_as_longlong(f) & 0x7fffffffffffffffull;
+        mb = b > mb ? b : mb;
+      }
+    atomicMax(&fmax_s, mb);
+    __syncthreads();
+    if (__longlong_as_double((long long)fmax_s) <= 7.450580596923828e-9) {
+      for (int r = warp; r < k; r += nw) {
+        const double drr = 0.5 * (1.0 + G[(int64_t)r * k + r]);
+        if (lane == 0) rdinv[r] = 1.0 / drr;
+        for (int c = lane; c < k; c += 32)
+          Rout[(int64_t)r * k + c] = c > r ? G[(int64_t)r * k + c] : (c == r ? drr : 0.0);
+      }
+      return;
+    }
+  }
   int attempt = 0;
   for (; attempt < 2; ++attempt) {
     if (tid == 0) {
@@ -413,49 +441,67 @@ chol_kernel(const double* __restrict__ G, int k, int64_t nrows, double* __restri
 }
 
 // V <- V R^{-1} in place (x R = v for every row v of V), R upper k x k with rdinv = 1/diag(R).
-// One warp per row; lane l holds entries l, l + 32, ... of the row in registers.  Skipped when
-// the factorisation that made R broke down.
-template <int KT>
+// One warp per RW rows; lane l holds entries l, l + 32, ... of each row in registers, and the
+// RW independent substitution chains are interleaved to hide their latency.  Skipped when the
+// factorisation that made R broke down.
+template <int KT, int RW>
 __global__ void __launch_bounds__(256)
 trsm_rows_kernel(double* __restrict__ V, int64_t ldv, int n, int k, const double* __restrict__ R,
                  const double* __restrict__ rdinv, const int* __restrict__ status) {
   if (*status & DEV_CHOL_BREAKDOWN) return;
   const int lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row >= n) return;
-  double* v = V + row * ldv;
-  double x[KT];
+  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RW;
+  if (row0 >= n) return;
+  double x[RW][KT];
 #pragma unroll
-  for (int t = 0; t < KT; ++t) {
-    const int l = 32 * t + lane;
-    x[t] = l < k ? v[l] : 0.0;
+  for (int w = 0; w < RW; ++w) {
+    const bool valid = row0 + w < n;
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int l = 32 * t + lane;
+      x[w][t] = (valid && l < k) ? V[(row0 + w) * ldv + l] : 0.0;
+    }
   }
 #pragma unroll
   for (int t = 0; t < KT; ++t) {
     const int jend = min(32, k - 32 * t);
     for (int jj = 0; jj < jend; ++jj) {
       const int j = 32 * t + jj;
-      const double xj = __shfl_sync(0xffffffffu, x[t], jj) * __ldg(rdinv + j);
-      if (lane == jj) x[t] = xj;
+      const double rd = __ldg(rdinv + j);
+      double xj[RW];
+#pragma unroll
+      for (int w = 0; w < RW; ++w) {
+        xj[w] = __shfl_sync(0xffffffffu, x[w][t], jj) * rd;
+        if (lane == jj) x[w][t] = xj[w];
+      }
       const double* Rj = R + (int64_t)j * k;
 #pragma unroll
       for (int t2 = t; t2 < KT; ++t2) {
         const int l = 32 * t2 + lane;
-        if (l > j && l < k) x[t2] = fma(-xj, __ldg(Rj + l), x[t2]);
+        if (l > j && l < k) {
+          const double r = __ldg(Rj + l);
+#pragma unroll
+          for (int w = 0; w < RW; ++w) x[w][t2] = fma(-xj[w], r, x[w][t2]);
+        }
       }
     }
   }
 #pragma unroll
-  for (int t = 0; t < KT; ++t) {
-    const int l = 32 * t + lane;
-    if (l < k) v[l] = x[t];
+  for (int w = 0; w < RW; ++w) {
+    if (row0 + w >= n) break;
+#pragma unroll
+    for (int t = 0; t < KT; ++t) {
+      const int l = 32 * t + lane;
+      if (l < k) V[(row0 + w) * ldv + l] = x[w][t];
+    }
   }
 }
 
 template <int KT>
 void launch_trsm(double* V, int64_t ldv, int n, int k, const double* R, const double* rdinv,
                  const int* status, cudaStream_t s) {
-  trsm_rows_kernel<KT><<<ceil_div(n, 8), 256, 0, s>>>(V, ldv, n, k, R, rdinv, status);
+  constexpr int RW = KT <= 6 ? 2 : 1;
+  trsm_rows_kernel<KT, RW><<<ceil_div(n, 8 * RW), 256, 0, s>>>(V, ldv, n, k, R, rdinv, status);
 }
 
 int trsm_rows(double* V, int64_t ldv, int n, int k, const double* R, const double* rdinv,
@@ -842,10 +888,12 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
                                                                    0x5EEDull + (uint64_t)n * 131 + J);
   TK_LAUNCH();
   TK_TRY(cholqr2(V, k, n, k, cw, s));
-  // Power steps before the first Rayleigh-Ritz solve (which on a random or stale block would
-  // buy nothing): V <- orth(normalise(M V) + 1e-3 V).  The small multiple of V keeps the block
-  // of full rank when M has fewer than k nonzero eigenvalues.
-  for (int rep = 0; rep < 4; ++rep) {
+  // Power steps before the first Rayleigh-Ritz solve (which on a random block would buy
+  // nothing): V <- orth(normalise(M V) + 1e-3 V).  The small multiple of V keeps the block of
+  // full rank when M has fewer than k nonzero eigenvalues.  (A warm start with a single power
+  // step costs more Rayleigh-Ritz iterations than the three steps it saves.)
+  const int power_steps = 4;
+  for (int rep = 0; rep < power_steps; ++rep) {
     double* W = T1.as<double>();
     if (use32)
       TK_TRY(gemm_nn_f32a(n, k, n, 1.0, M32, n, V, k, 0.0, nullptr, 0, 0.0, nullptr, 0, W, k, s));
@@ -897,7 +945,6 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     TK_LAUNCH();
     TK_CUDA(cudaMemcpyAsync(th.data(), evh.p, sizeof(double) * ka, cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaMemcpyAsync(rr.data(), rn.p, sizeof(double) * ka, cudaMemcpyDeviceToHost, s));
-    TK_CUDA(cudaStreamSynchronize(s));
     theta1 = std::max(theta1, th[0]);
     const double thr = tol * std::max(theta1, 1e-300);
     int nlock = 0;

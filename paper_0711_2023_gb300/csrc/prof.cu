@@ -24,6 +24,7 @@ std::vector<Rec> g_recs;
 
 void clear_locked() {
   for (auto& r : g_recs) {
+    if (!r.a) continue;  // a counter has no events
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }

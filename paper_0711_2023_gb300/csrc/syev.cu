@@ -32,14 +32,12 @@ namespace {
 
 constexpr int JAC32_MAX_H = SYEV_REFINED_MAX_M / 2;
 
-__device__ __forceinline__ int rr_slot(int j, int r, int m) {
-  return j == 0 ? 0 : 1 + (j - 1 + r) % (m - 1);
-}
 
 // Cyclic Jacobi on FP32(0.5 (A + A^T)) in shared memory (scaled by a power of two when its
 // entries lie outside FP32's comfortable range), round-robin ordering: round r rotates the m/2
 // disjoint pairs at once.  A rotation is applied when |a_pq| exceeds both tol_abs * max |a_ii|
-// and tol_rel * sqrt|a_pp a_qq|; the sweep loop ends after a sweep without one.  The
+// and tol_rel * sqrt|a_pp a_qq|; the sweep loop ends after a sweep without one, or once a
+// sweep fails to halve the off-diagonal mass (the FP32 rounding floor).  The
 // update is in place: block (I, K) of J^T A J reads and writes only rows {p_I, q_I} x columns
 // {p_K, q_K}, which no other block touches.  Q is kept transposed so that the rows of a pair's
 // two columns are contiguous for the lanes.  X (m x m, FP64, ld ldx) receives Q.
@@ -55,7 +53,7 @@ jacobi32_kernel(const double* __restrict__ A, int m, int64_t lda, float tol_rel,
   __shared__ float dmax_s;
   __shared__ unsigned long long amax_s;
   __shared__ double pow2_s;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // max |a_ij| from the bit patterns (integer compares keep this off the FP64 pipe)
   if (tid == 0) amax_s = 0ull;
   __syncthreads();
@@ -98,20 +96,34 @@ jacobi32_kernel(const double* __restrict__ A, int m, int64_t lda, float tol_rel,
   }
   __syncthreads();
   const float abs_thr = tol_abs * dmax_s;
+  // Fixed work assignment of the update phase (no divisions inside the sweep loop).
+  const int sa = blockDim.x / h, kb = tid % h, ib = tid / h;
+  const int sq = blockDim.x / mp, rq = tid % mp, iq = tid / mp;
+  __shared__ float off_s;
+  float prev_off2 = 3.0e38f;
   int sweep = 0, converged = 0;
   for (; sweep < max_sweeps; ++sweep) {
     int active_sweep = 0;
-    for (int r = 0; r < mp - 1; ++r) {
+    // Round-robin slots of pair tid (slot 0 stays, the others step through 1..mp-1).
+    int sx = tid == 0 ? 0 : 1 + (tid - 1) % (mp - 1);
+    int sy = 1 + (mp - 2 - tid) % (mp - 1);
+    for (int r = 0; r < mp - 1; ++r, sx = (sx == 0 ? 0 : (sx == mp - 1 ? 1 : sx + 1)),
+                                     sy = (sy == mp - 1 ? 1 : sy + 1)) {
       int on = 0;
       if (tid < h) {
-        const int x = rr_slot(tid, r, mp), y = rr_slot(mp - 1 - tid, r, mp);
+        const int x = sx, y = sy;
         const int p = min(x, y), q = max(x, y);
         const float app = a[p * mp + p], aqq = a[q * mp + q], apq = a[p * mp + q];
         float c = 1.0f, s = 0.0f, np_ = app, nq_ = aqq;
         if (fabsf(apq) > abs_thr && fabsf(apq) > tol_rel * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
           // Symmetric 2x2 Schur decomposition (Golub & Van Loan, Algorithm 8.4.1).
-          const float tau = (aqq - app) / (2.0f * apq);
-          const float t = copysignf(1.0f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+          // Approximate division and square root suffice: any (c, s) with c^2 + s^2 = 1 to
+          // FP32 precision is a rotation, and the FP64 refinement removes what it leaves.
+          const float tau = __fdividef(aqq - app, 2.0f * apq);
+          const float w = fmaf(tau, tau, 1.0f);
+          const float t = fabsf(tau) < 1e18f
+                              ? copysignf(__frcp_rn(fabsf(tau) + w * rsqrtf(w)), tau)
+                              : __frcp_rn(2.0f * tau);
           c = rsqrtf(fmaf(t, t, 1.0f));
           s = t * c;
           np_ = app - t * apq;
@@ -123,10 +135,14 @@ jacobi32_kernel(const double* __restrict__ A, int m, int64_t lda, float tol_rel,
       }
       if (!__syncthreads_or(on)) continue;  // nothing to rotate this round (uniform)
       active_sweep = 1;
-      for (int I = warp; I < h; I += nw) {
-        const float c1 = cs[I], s1 = sn[I];
-        const int p = pi[I], q = qi[I];
-        for (int K = lane; K < h; K += 32) {
+      // 2x2 blocks (I, K): thread t takes K = t mod h and I = t / h, t / h + sa, ...
+      if (tid < sa * h) {
+        const int K = kb;
+        const float c2 = cs[K], s2 = sn[K];
+        const int u = pi[K], v = qi[K];
+        for (int I = ib; I < h; I += sa) {
+          const float c1 = cs[I], s1 = sn[I];
+          const int p = pi[I], q = qi[I];
           if (K == I) {
             if (on_s[I]) {
               a[p * mp + p] = dp[I];
@@ -136,9 +152,7 @@ jacobi32_kernel(const double* __restrict__ A, int m, int64_t lda, float tol_rel,
             }
             continue;
           }
-          const float c2 = cs[K], s2 = sn[K];
           if (s1 == 0.0f && s2 == 0.0f) continue;
-          const int u = pi[K], v = qi[K];
           const float x0 = a[p * mp + u], x1 = a[p * mp + v];
           const float x2 = a[q * mp + u], x3 = a[q * mp + v];
           const float rpu = c1 * x0 - s1 * x2, rpv = c1 * x1 - s1 * x3;
@@ -148,18 +162,44 @@ jacobi32_kernel(const double* __restrict__ A, int m, int64_t lda, float tol_rel,
           a[q * mp + u] = c2 * rqu - s2 * rqv;
           a[q * mp + v] = s2 * rqu + c2 * rqv;
         }
-        if (s1 != 0.0f) {
-          // Q <- Q J: columns p and q of Q are rows p and q of qt.
-          for (int row = lane; row < mp; row += 32) {
-            const float y0 = qt[p * mp + row], y1 = qt[q * mp + row];
-            qt[p * mp + row] = c1 * y0 - s1 * y1;
-            qt[q * mp + row] = s1 * y0 + c1 * y1;
-          }
+      }
+      // Q <- Q J: thread t takes row t mod mp of the column pairs I = t / mp, t / mp + sq, ...
+      // (columns p and q of Q are rows p and q of qt: consecutive threads, consecutive words).
+      if (tid < sq * mp) {
+        for (int I = iq; I < h; I += sq) {
+          const float c1 = cs[I], s1 = sn[I];
+          if (s1 == 0.0f) continue;
+          const int p = pi[I], q = qi[I];
+          const float y0 = qt[p * mp + rq], y1 = qt[q * mp + rq];
+          qt[p * mp + rq] = c1 * y0 - s1 * y1;
+          qt[q * mp + rq] = s1 * y0 + c1 * y1;
         }
       }
       __syncthreads();
     }
     if (!active_sweep) {
+      converged = 1;
+      ++sweep;
+      break;
+    }
+    // Off-diagonal mass after the sweep.  Jacobi converges quadratically until FP32 rounding
+    // sets a floor; a sweep that does not halve the mass has reached it, and the FP64
+    // refinement takes over from there.
+    if (tid == 0) off_s = 0.0f;
+    __syncthreads();
+    float o2 = 0.0f;
+    for (int t = tid; t < mp * mp; t += blockDim.x) {
+      const int r = t / mp, c = t - r * mp;
+      if (r != c) o2 = fmaf(a[t], a[t], o2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) o2 += __shfl_xor_sync(0xffffffffu, o2, o);
+    if (lane == 0) atomicAdd(&off_s, o2);
+    __syncthreads();
+    const float off2 = off_s;
+    const bool stalled = sweep >= 2 && off2 > 0.25f * prev_off2;
+    prev_off2 = off2;
+    if (stalled) {
       converged = 1;
       ++sweep;
       break;
@@ -286,8 +326,11 @@ int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* eval
         jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)(2 * sizeof(float) * SYEV_REFINED_MAX_M * SYEV_REFINED_MAX_M));
     TK_CUDA(attr);
-    jacobi32_kernel<<<1, 1024, smem, s>>>(A, m, lda, 1e-6f, 1e-7f, 40, cur + m, ld,
-                                          info.as<int>());
+    {
+      ProfScope pj("syev_jacobi32", s, 0.0, 0.0);
+      jacobi32_kernel<<<1, 1024, smem, s>>>(A, m, lda, 1e-6f, 1e-7f, 40, cur + m, ld,
+                                            info.as<int>());
+    }
     TK_LAUNCH();
   }
   // Refinement.  The statistics are read back (one host synchronisation each) from the step
@@ -345,6 +388,7 @@ int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* eval
   TK_CUDA(cudaMemcpyAsync(hinfo, info.p, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
   st->fp32_sweeps = hinfo[0];
+  prof_count("syev_fp32_sweeps", (double)hinfo[0]);
   prof_count("syev_steps", (double)step);
   if (!accepted) {
     st->fallback = true;
