@@ -47,6 +47,7 @@ def load_peaks():
 
 # FP64 SIMT peak of GB300: 1.25 TFLOP/s (nominal FP64 rate of the part; no measured figure).
 FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # nominal: SMs x FP32 lanes x 2 x max clock
 
 
 class ClockSampler:
@@ -197,6 +198,16 @@ STAGES = ("eig_topk", "syev_refined", "syev_jacobi32")   # spans that contain ma
 COUNTERS = ("eig_outer", "syev_steps", "syev_fp32_sweeps", "syev_fallback")   # iteration counts of the eigensolver
 
 
+# DRAM traffic over algorithmic bytes per launch, from one ncu capture of each kernel on the
+# 500^3 workload (dram__bytes_read.sum + dram__bytes_write.sum; profiles/syrk_f64_500cube_hooi.md
+# and profiles/gram_bf16x3_500cube.md).  The traffic of a bench launch is this ratio times its
+# algorithmic bytes: the traffic of both kernels grows with the rows x K of the projection read.
+NCU_TRAFFIC_RATIO = {
+    "syrk_f64": 10.034e6 / (8.0 * 500 * 2500 + 8.0 * 500 * 500),
+    "gram_bf16x3": 178.65e6 / (4.0 * 500 * 50000 + 8.0 * 500 * 500),
+}
+
+
 def roofline_of(prof, name, total_ms, bound, peak, unit, peak_source, per="flops"):
     d = prof.get(name)
     if not d:
@@ -205,8 +216,13 @@ def roofline_of(prof, name, total_ms, bound, peak, unit, peak_source, per="flops
     work = (d["flops"] if per == "flops" else d["bytes"]) / d["launches"]
     scale = 1e12 if unit == "TFLOP/s" else 1e9
     achieved = work / (per_launch_ms * 1e-3) / scale if per_launch_ms else 0.0
+    ratio = NCU_TRAFFIC_RATIO.get(name)
+    traffic = ratio * d["bytes"] / d["launches"] if ratio else None
     return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None, "peak_source": peak_source,
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_note": ("bytes per launch: ncu DRAM bytes / algorithmic bytes of a 500^3 "
+                             "capture x this launch's algorithmic bytes") if ratio else None,
+            "algorithmic_bytes": d["bytes"] / d["launches"], "peak_source": peak_source,
             "share_of_step": d["ms"] / total_ms, "launches": d["launches"]}
 
 
@@ -421,8 +437,17 @@ def main():
     kp = kernels_only(prof)
     dom = max(kp, key=lambda k: kp[k]["ms"])
     roofline = roofline_of(prof, dom, total_ms, "alu", FP64_PEAK_TFLOPS, "TFLOP/s", fp64_src)
-    tt = prof.get("ttmc_f64")
-    ttmc_gbs = tt["bytes"] / (tt["ms"] * 1e-3) / 1e9 if tt and tt["ms"] else None
+    def ttmc_rates(pr, name, flop_peak):
+        d = pr.get(name)
+        if not d or not d["ms"]:
+            return None
+        secs = d["ms"] * 1e-3
+        gbs, tfs = d["bytes"] / secs / 1e9, d["flops"] / secs / 1e12
+        return {"kernel": name, "launches": d["launches"], "ms_per_launch": d["ms"] / d["launches"],
+                "algorithmic_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs")
+                else None, "tflops": tfs, "frac_alu": tfs / flop_peak,
+                "note": "HOOI projection; at core 50 it does J_m J_o FMAs per fiber against 12 "
+                        "bytes of index data, so it is bound by arithmetic and row gathers, not HBM"}
     bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
     mx_gram = roofline_of(mx_prof, "gram_bf16x3", mx_ms, "tensor", bf16, "TFLOP/s",
                           f"{peak_src} bf16 sustained (cuBLAS), algorithmic FP32-equivalent "
@@ -449,7 +474,8 @@ def main():
         "fits": fits,
         "kernels": kern_table(prof, total_ms),
         "eig_counters": prof["counters"],
-        "ttmc_f64_gbs": ttmc_gbs,
+        "ttmc": {"fp64": ttmc_rates(prof, "ttmc_f64", FP64_PEAK_TFLOPS),
+                 "mixed": ttmc_rates(mx_prof, "ttmc_mixed", FP32_PEAK_TFLOPS)},
         "roofline": roofline,
         "mixed": {"value": mx_value, "unit": "sweeps/s", "ms_per_step": mx_ms / args.steps,
                   "speedup_vs_fp64": mx_value / value,

@@ -114,8 +114,9 @@ ttmc_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __restric
 }
 
 // One CTA per root slice i_n of ordering (n, o, m); warps take the slice's fibers (i_n, i_o) in
-// turn.  Each warp also zero-fills the columns of the i_o values between its fiber and the
-// previous one, so every element of row i_n (including the padding) is written exactly once.
+// turn, summing each fiber's leaves in index order.  Each warp also zero-fills the columns of
+// the i_o values between its fiber and the previous one, so every element of row i_n
+// (including the padding) is written exactly once.
 template <int NP>
 __global__ void __launch_bounds__(256)
 slice_proj_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __restrict__ fiber_idx,
@@ -154,13 +155,21 @@ slice_proj_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __r
       float acc[NP];
 #pragma unroll
       for (int r = 0; r < NP; ++r) acc[r] = 0.f;
-      for (int64_t l = l0; l < l1; ++l) {
-        const float x = val[l];
-        const float* row = Um + (int64_t)leaf_idx[l] * Jm + pc;
+      // Up to 32 leaves at a time: one coalesced load of their indices and values, then the
+      // row gathers, which are independent of one another and so overlap.
+      for (int64_t lb = l0; lb < l1; lb += 32) {
+        const int cnt = (int)min64(32, l1 - lb);
+        const int my_idx = lane < cnt ? leaf_idx[lb + lane] : 0;
+        const float my_val = lane < cnt ? val[lb + lane] : 0.f;
+#pragma unroll(NP <= 4 ? 4 : 2)
+        for (int j = 0; j < cnt; ++j) {
+          const float x = __shfl_sync(0xffffffffu, my_val, j);
+          const float* row = Um + (int64_t)__shfl_sync(0xffffffffu, my_idx, j) * Jm + pc;
 #pragma unroll
-        for (int r = 0; r < NP; ++r) {
-          const int p = lane + 32 * r;
-          if (pc + p < Jm) acc[r] = fmaf(x, row[p], acc[r]);
+          for (int r = 0; r < NP; ++r) {
+            const int p = lane + 32 * r;
+            if (pc + p < Jm) acc[r] = fmaf(x, row[p], acc[r]);
+          }
         }
       }
 #pragma unroll
