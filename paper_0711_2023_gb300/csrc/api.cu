@@ -177,7 +177,7 @@ int alloc_buffers(Run& r) {
   const int* J = r.J;
   for (int a = 0; a < 3; ++a) {
     TK_TRY(r.U[a].alloc(sizeof(double) * r.dim(a) * J[a], r.s));
-    if (r.mixed) TK_TRY(r.U32[a].alloc(sizeof(float) * r.dim(a) * J[a], r.s));
+    if (r.mixed) TK_TRY(r.U32[a].alloc(sizeof(float) * r.dim(a) * factor_ld32(J[a]), r.s));
   }
   const int64_t maxI = std::max(r.dim(0), std::max(r.dim(1), r.dim(2)));
   TK_TRY(r.M.alloc(sizeof(double) * maxI * maxI, r.s));
@@ -224,7 +224,8 @@ int alloc_buffers(Run& r) {
 
 int refresh32(Run& r, int n) {
   if (!r.mixed) return TUCKER_OK;
-  return f64_to_f32(r.U[n].as<double>(), r.U32[n].as<float>(), r.dim(n) * r.J[n], r.s);
+  return f64_to_f32_rows(r.U[n].as<double>(), r.dim(n), r.J[n], r.U32[n].as<float>(),
+                         factor_ld32(r.J[n]), r.s);
 }
 
 int eig_update(Run& r, int n, bool warm) {
@@ -272,8 +273,9 @@ int hooi_matrix(Run& r, int n) {
   }
   const int64_t ld = gram_ld(K);
   __nv_bfloat16 *yh = r.Yh.as<__nv_bfloat16>(), *yl = r.Yl.as<__nv_bfloat16>();
-  TK_TRY(ttmc_mixed(r.X, ord, r.U32[m].as<float>(), r.J[m], r.U32[o].as<float>(), r.J[o], yh, yl,
-                    ld, n == 2 ? r.Y32.as<float>() : nullptr, r.s));
+  TK_TRY(ttmc_mixed(r.X, ord, r.U32[m].as<float>(), factor_ld32(r.J[m]), r.J[m],
+                    r.U32[o].as<float>(), factor_ld32(r.J[o]), r.J[o], yh, yl, ld,
+                    n == 2 ? r.Y32.as<float>() : nullptr, r.s));
   GramTerm t{yh, yl, K, ld};
   return gram_bf16x3((int)r.dim(n), 1, &t, r.M.as<double>(), r.s);
 }
@@ -293,7 +295,8 @@ int slice_term(Run& r, int n, int m, int which, GramTerm* t) {
   const int64_t ld = gram_ld(K);
   __nv_bfloat16* yh = which == 0 ? r.Yh.as<__nv_bfloat16>() : r.Y2h.as<__nv_bfloat16>();
   __nv_bfloat16* yl = which == 0 ? r.Yl.as<__nv_bfloat16>() : r.Y2l.as<__nv_bfloat16>();
-  TK_TRY(slice_proj_mixed(r.X, ord, r.U32[m].as<float>(), r.J[m], yh, yl, ld, r.s));
+  TK_TRY(slice_proj_mixed(r.X, ord, r.U32[m].as<float>(), factor_ld32(r.J[m]), r.J[m], yh, yl,
+                          ld, r.s));
   *t = GramTerm{yh, yl, K, ld};
   return TUCKER_OK;
 }
@@ -321,8 +324,9 @@ int core_and_fit(Run& r, bool w_ready, double* fit, double* g2) {
                       r.Y.as<double>(), r.s));
   } else {
     if (!w_ready)
-      TK_TRY(ttmc_mixed(r.X, ord, r.U32[0].as<float>(), r.J[0], r.U32[1].as<float>(), r.J[1],
-                        nullptr, nullptr, 0, r.Y32.as<float>(), r.s));
+      TK_TRY(ttmc_mixed(r.X, ord, r.U32[0].as<float>(), factor_ld32(r.J[0]), r.J[0],
+                        r.U32[1].as<float>(), factor_ld32(r.J[1]), r.J[1], nullptr, nullptr, 0,
+                        r.Y32.as<float>(), r.s));
     TK_TRY(f32_to_f64(r.Y32.as<float>(), r.Y.as<double>(), nW, r.s));
   }
   TK_TRY(core_from_ttmc3(r.Y.as<double>(), (int)r.dim(2), r.J[0], r.J[1], r.U[2].as<double>(),
@@ -747,8 +751,8 @@ int tucker_ttmc_mixed(tucker_tensor X, int32_t n, const float* d_Um, int32_t Jm,
   Ordering* ord;
   TK_TRY(ensure_ordering(X, n, m, o, s, &ord));
   TK_TRY(ensure_val_f32(X, ord, s));
-  TK_TRY(ttmc_mixed(X, ord, d_Um, Jm, d_Uo, Jo, (__nv_bfloat16*)d_Yhi, (__nv_bfloat16*)d_Ylo, ldY,
-                    d_Y32, s));
+  TK_TRY(ttmc_mixed(X, ord, d_Um, Jm, Jm, d_Uo, Jo, Jo, (__nv_bfloat16*)d_Yhi,
+                    (__nv_bfloat16*)d_Ylo, ldY, d_Y32, s));
   TK_CUDA(cudaStreamSynchronize(s));
   return TUCKER_OK;
 }
@@ -763,7 +767,8 @@ int tucker_slice_proj_mixed(tucker_tensor X, int32_t n, int32_t m, const float* 
   Ordering* ord;
   TK_TRY(ensure_ordering(X, n, o, m, s, &ord));
   TK_TRY(ensure_val_f32(X, ord, s));
-  TK_TRY(slice_proj_mixed(X, ord, d_Um, Jm, (__nv_bfloat16*)d_Yhi, (__nv_bfloat16*)d_Ylo, ldY, s));
+  TK_TRY(slice_proj_mixed(X, ord, d_Um, Jm, Jm, (__nv_bfloat16*)d_Yhi, (__nv_bfloat16*)d_Ylo, ldY,
+                          s));
   TK_CUDA(cudaStreamSynchronize(s));
   return TUCKER_OK;
 }

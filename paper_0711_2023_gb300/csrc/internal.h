@@ -80,11 +80,17 @@ int scale_f64(int64_t n, double alpha, double* x, cudaStream_t s);
 // mixed.cu (FP32 projections written as BF16 hi/lo pairs for the tensor-core Gram)
 int f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 int f32_to_f64(const float* a, double* b, int64_t n, cudaStream_t s);
-int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int Jm,
-               const float* Uo, int Jo, __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY,
-               float* Y32, cudaStream_t s);
-int slice_proj_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int Jm,
-                     __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, cudaStream_t s);
+// a (rows x cols, dense) to FP32 rows of stride ldb >= cols, padding columns zeroed.
+int f64_to_f32_rows(const double* a, int64_t rows, int cols, float* b, int64_t ldb,
+                    cudaStream_t s);
+// Factor row strides ldm, ldo (in floats).  Rows padded to a multiple of 4 floats, 16-byte
+// aligned, let the slice projection load them as float4 (factor_ld32 gives that stride).
+inline int64_t factor_ld32(int J) { return (J + 3) / 4 * 4; }
+int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int64_t ldm, int Jm,
+               const float* Uo, int64_t ldo, int Jo, __nv_bfloat16* Yh, __nv_bfloat16* Yl,
+               int64_t ldY, float* Y32, cudaStream_t s);
+int slice_proj_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int64_t ldm,
+                     int Jm, __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, cudaStream_t s);
 
 // gram_tc.cu: M = sum_t Y_t Y_t^T on tcgen05 with Y_t = hi + lo (BF16x3), FP64 result.
 struct GramTerm {

@@ -26,21 +26,31 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restric
   if (t < n) b[t] = (float)a[t];
 }
 
+// b (rows x ldb) = FP32 of a (rows x cols, dense), zeros in columns cols..ldb-1.
+__global__ void f64_to_f32_rows_kernel(const double* __restrict__ a, int64_t rows, int cols,
+                                       float* __restrict__ b, int64_t ldb) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * ldb) return;
+  const int64_t r = t / ldb, c = t - r * ldb;
+  b[t] = c < cols ? (float)a[r * cols + c] : 0.f;
+}
+
 __global__ void f32_to_f64_kernel(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) b[t] = (double)a[t];
 }
 
-template <int AP, int AQ>
+template <int AP, int AQ, bool VEC>
 __global__ void __launch_bounds__(256)
 ttmc_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __restrict__ fiber_idx,
                   const int64_t* __restrict__ fiber_ptr, const int32_t* __restrict__ leaf_idx,
-                  const float* __restrict__ val, const float* __restrict__ Um, int Jm,
-                  const float* __restrict__ Uo, int Jo, __nv_bfloat16* __restrict__ Yh,
-                  __nv_bfloat16* __restrict__ Yl, int64_t ldY, float* __restrict__ Y32) {
+                  const float* __restrict__ val, const float* __restrict__ Um, int64_t ldm,
+                  int Jm, const float* __restrict__ Uo, int64_t ldo, int Jo,
+                  __nv_bfloat16* __restrict__ Yh, __nv_bfloat16* __restrict__ Yl, int64_t ldY,
+                  float* __restrict__ Y32) {
   constexpr int TP = 16 * AP, TQ = 16 * AQ, FC = 64, RQ = (TQ + 31) / 32;
   __shared__ float su[FC][TP];
-  __shared__ float st[FC][TQ];
+  __shared__ __align__(16) float st[FC][TQ];
   const int i = blockIdx.x;
   const int p0 = blockIdx.y * TP, q0 = blockIdx.z * TQ;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -53,28 +63,78 @@ ttmc_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __restric
   const int64_t fb = root_ptr[i], fe = root_ptr[i + 1];
   for (int64_t fc = fb; fc < fe; fc += FC) {
     const int nc = (int)min64(FC, fe - fc);
-    for (int c = warp; c < nc; c += 8) {
-      const int64_t f = fc + c;
-      const int64_t l0 = fiber_ptr[f], l1 = fiber_ptr[f + 1];
-      const int64_t im = fiber_idx[f];
-      for (int tp = lane; tp < TP; tp += 32)
-        su[c][tp] = (p0 + tp < Jm) ? Um[im * Jm + p0 + tp] : 0.f;
-      float t[RQ];
+    if constexpr (VEC) {
+      // Factor rows padded to a multiple of 4 floats and TQ = 64: a group of 8 lanes owns one
+      // fiber (four per warp at once) and loads each leaf's 64-column row segment of U_o with
+      // two float4 loads per lane; the leaves' indices and values come 8 at a time.
+      const int gid = lane >> 3, gl = lane & 7;
+      const bool in0 = q0 + 4 * gl < ldo, in1 = q0 + 4 * (gl + 8) < ldo;
+      for (int c0 = warp * 4; c0 < nc; c0 += 32) {
+        const int c = c0 + gid;
+        const bool active = c < nc;
+        int64_t l0 = 0;
+        int len = 0;
+        if (active) {
+          const int64_t f = fc + c;
+          l0 = fiber_ptr[f];
+          len = (int)(fiber_ptr[f + 1] - l0);
+          const int64_t im = fiber_idx[f];
+          for (int tp = gl; tp < TP; tp += 8)
+            su[c][tp] = (p0 + tp < Jm) ? Um[im * ldm + p0 + tp] : 0.f;
+        }
+        const int maxlen = __reduce_max_sync(0xffffffffu, len);
+        float r[8];
 #pragma unroll
-      for (int r = 0; r < RQ; ++r) t[r] = 0.f;
-      for (int64_t l = l0; l < l1; ++l) {
-        const float x = val[l];
-        const float* row = Uo + (int64_t)leaf_idx[l] * Jo + q0;
+        for (int q = 0; q < 8; ++q) r[q] = 0.f;
+        for (int lb = 0; lb < maxlen; lb += 8) {
+          const bool have = lb + gl < len;
+          const int my_idx = have ? leaf_idx[l0 + lb + gl] : 0;
+          const float my_val = have ? val[l0 + lb + gl] : 0.f;
+          const int cnt = min(8, maxlen - lb);
+#pragma unroll 4
+          for (int j = 0; j < cnt; ++j) {
+            const int idx = __shfl_sync(0xffffffffu, my_idx, j, 8);
+            const float x = __shfl_sync(0xffffffffu, my_val, j, 8);
+            if (lb + j < len) {
+              const float4* row = reinterpret_cast<const float4*>(Uo + (int64_t)idx * ldo + q0);
+              const float4 u0 = in0 ? row[gl] : make_float4(0.f, 0.f, 0.f, 0.f);
+              const float4 u1 = in1 ? row[gl + 8] : make_float4(0.f, 0.f, 0.f, 0.f);
+              r[0] = fmaf(x, u0.x, r[0]); r[1] = fmaf(x, u0.y, r[1]);
+              r[2] = fmaf(x, u0.z, r[2]); r[3] = fmaf(x, u0.w, r[3]);
+              r[4] = fmaf(x, u1.x, r[4]); r[5] = fmaf(x, u1.y, r[5]);
+              r[6] = fmaf(x, u1.z, r[6]); r[7] = fmaf(x, u1.w, r[7]);
+            }
+          }
+        }
+        if (active) {
+          *reinterpret_cast<float4*>(&st[c][4 * gl]) = make_float4(r[0], r[1], r[2], r[3]);
+          *reinterpret_cast<float4*>(&st[c][4 * (gl + 8)]) = make_float4(r[4], r[5], r[6], r[7]);
+        }
+      }
+    } else {
+      for (int c = warp; c < nc; c += 8) {
+        const int64_t f = fc + c;
+        const int64_t l0 = fiber_ptr[f], l1 = fiber_ptr[f + 1];
+        const int64_t im = fiber_idx[f];
+        for (int tp = lane; tp < TP; tp += 32)
+          su[c][tp] = (p0 + tp < Jm) ? Um[im * ldm + p0 + tp] : 0.f;
+        float t[RQ];
+#pragma unroll
+        for (int r = 0; r < RQ; ++r) t[r] = 0.f;
+        for (int64_t l = l0; l < l1; ++l) {
+          const float x = val[l];
+          const float* row = Uo + (int64_t)leaf_idx[l] * ldo + q0;
+#pragma unroll
+          for (int r = 0; r < RQ; ++r) {
+            const int q = lane + 32 * r;
+            if (q < TQ && q0 + q < Jo) t[r] = fmaf(x, row[q], t[r]);
+          }
+        }
 #pragma unroll
         for (int r = 0; r < RQ; ++r) {
           const int q = lane + 32 * r;
-          if (q < TQ && q0 + q < Jo) t[r] = fmaf(x, row[q], t[r]);
+          if (q < TQ) st[c][q] = t[r];
         }
-      }
-#pragma unroll
-      for (int r = 0; r < RQ; ++r) {
-        const int q = lane + 32 * r;
-        if (q < TQ) st[c][q] = t[r];
       }
     }
     __syncthreads();
@@ -113,6 +173,36 @@ ttmc_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __restric
   }
 }
 
+// Row i of an SP/MP projection when slice i has no nonzeros: all zeros (one CTA).
+__device__ __forceinline__ void zero_row(__nv_bfloat16* rh, __nv_bfloat16* rl, int64_t ldY) {
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  for (int64_t c = threadIdx.x; c < ldY; c += blockDim.x) {
+    rh[c] = z;
+    rl[c] = z;
+  }
+}
+
+// The columns that belong to no fiber, written as zeros by the warp of the next fiber: those of
+// the i_o values between fiber f - 1 and fiber f, and after the slice's last fiber those up to
+// the padded row length.
+__device__ __forceinline__ void zero_gaps(const int32_t* __restrict__ fiber_idx, int64_t f,
+                                          int64_t fb, int64_t fe, int64_t io, int Jm,
+                                          __nv_bfloat16* rh, __nv_bfloat16* rl, int64_t ldY,
+                                          int lane) {
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  const int64_t gap0 = (f == fb) ? 0 : (int64_t)(fiber_idx[f - 1] + 1) * Jm;
+  for (int64_t c = gap0 + lane; c < io * Jm; c += 32) {
+    rh[c] = z;
+    rl[c] = z;
+  }
+  if (f == fe - 1) {
+    for (int64_t c = (io + 1) * Jm + lane; c < ldY; c += 32) {
+      rh[c] = z;
+      rl[c] = z;
+    }
+  }
+}
+
 // One CTA per root slice i_n of ordering (n, o, m); warps take the slice's fibers (i_n, i_o) in
 // turn, summing each fiber's leaves in index order.  Each warp also zero-fills the columns of
 // the i_o values between its fiber and the previous one, so every element of row i_n
@@ -121,35 +211,21 @@ template <int NP>
 __global__ void __launch_bounds__(256)
 slice_proj_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __restrict__ fiber_idx,
                         const int64_t* __restrict__ fiber_ptr, const int32_t* __restrict__ leaf_idx,
-                        const float* __restrict__ val, const float* __restrict__ Um, int Jm,
-                        int64_t Io, __nv_bfloat16* __restrict__ Yh, __nv_bfloat16* __restrict__ Yl,
+                        const float* __restrict__ val, const float* __restrict__ Um, int64_t ldm,
+                        int Jm, __nv_bfloat16* __restrict__ Yh, __nv_bfloat16* __restrict__ Yl,
                         int64_t ldY) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t i = blockIdx.x;
   __nv_bfloat16* rh = Yh + i * ldY;
   __nv_bfloat16* rl = Yl + i * ldY;
-  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
   const int64_t fb = root_ptr[i], fe = root_ptr[i + 1];
   if (fb == fe) {
-    for (int64_t c = threadIdx.x; c < ldY; c += blockDim.x) {
-      rh[c] = z;
-      rl[c] = z;
-    }
+    zero_row(rh, rl, ldY);
     return;
   }
   for (int64_t f = fb + warp; f < fe; f += nw) {
     const int64_t io = fiber_idx[f];
-    const int64_t gap0 = (f == fb) ? 0 : (int64_t)(fiber_idx[f - 1] + 1) * Jm;
-    for (int64_t c = gap0 + lane; c < io * Jm; c += 32) {
-      rh[c] = z;
-      rl[c] = z;
-    }
-    if (f == fe - 1) {
-      for (int64_t c = (io + 1) * Jm + lane; c < ldY; c += 32) {
-        rh[c] = z;
-        rl[c] = z;
-      }
-    }
+    zero_gaps(fiber_idx, f, fb, fe, io, Jm, rh, rl, ldY, lane);
     const int64_t l0 = fiber_ptr[f], l1 = fiber_ptr[f + 1];
     for (int pc = 0; pc < Jm; pc += 32 * NP) {
       float acc[NP];
@@ -161,10 +237,10 @@ slice_proj_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __r
         const int cnt = (int)min64(32, l1 - lb);
         const int my_idx = lane < cnt ? leaf_idx[lb + lane] : 0;
         const float my_val = lane < cnt ? val[lb + lane] : 0.f;
-#pragma unroll(NP <= 4 ? 4 : 2)
+#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
           const float x = __shfl_sync(0xffffffffu, my_val, j);
-          const float* row = Um + (int64_t)__shfl_sync(0xffffffffu, my_idx, j) * Jm + pc;
+          const float* row = Um + (int64_t)__shfl_sync(0xffffffffu, my_idx, j) * ldm + pc;
 #pragma unroll
           for (int r = 0; r < NP; ++r) {
             const int p = lane + 32 * r;
@@ -181,14 +257,124 @@ slice_proj_mixed_kernel(const int64_t* __restrict__ root_ptr, const int32_t* __r
   }
 }
 
+
+// The same projection for factor rows padded to a multiple of 4 floats (16-byte aligned) and
+// J_m <= 8 G = 64 (G = 8) or 128 (G = 16).  A group of G lanes owns one fiber (a warp takes
+// 32 / G fibers at once): its lanes hold the fiber's sum for columns 4 l .. 4 l + 3 and
+// 4 (l + G) .. + 3, load each leaf's factor row with two float4 loads, and take the fiber's leaf
+// indices and values G at a time with one coalesced load.  The per-fiber work (pointers, gap
+// zeroing, the BF16 split stores) is spread over the warp's fibers; leaves are summed in index
+// order, so the result is reproducible.
+template <int G>
+__global__ void __launch_bounds__(256)
+slice_proj_mixed_vec_kernel(const int64_t* __restrict__ root_ptr,
+                            const int32_t* __restrict__ fiber_idx,
+                            const int64_t* __restrict__ fiber_ptr,
+                            const int32_t* __restrict__ leaf_idx, const float* __restrict__ val,
+                            const float* __restrict__ Um, int64_t ldm, int Jm,
+                            __nv_bfloat16* __restrict__ Yh, __nv_bfloat16* __restrict__ Yl,
+                            int64_t ldY) {
+  constexpr int NF = 32 / G;  // fibers per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gid = lane / G, gl = lane % G;
+  const int64_t i = blockIdx.x;
+  __nv_bfloat16* rh = Yh + i * ldY;
+  __nv_bfloat16* rl = Yl + i * ldY;
+  const int64_t fb = root_ptr[i], fe = root_ptr[i + 1];
+  if (fb == fe) {
+    zero_row(rh, rl, ldY);
+    return;
+  }
+  const bool in0 = 4 * gl < ldm, in1 = 4 * (gl + G) < ldm;
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  for (int64_t f0 = fb + (int64_t)warp * NF; f0 < fe; f0 += (int64_t)nw * NF) {
+    const int64_t f = f0 + gid;
+    const bool active = f < fe;
+    int64_t io = 0, l0 = 0;
+    int len = 0;
+    if (active) {
+      io = fiber_idx[f];
+      l0 = fiber_ptr[f];
+      len = (int)(fiber_ptr[f + 1] - l0);
+      // columns of the i_o values between the previous fiber and this one, and after the last
+      const int64_t gap0 = (f == fb) ? 0 : (int64_t)(fiber_idx[f - 1] + 1) * Jm;
+      for (int64_t c = gap0 + gl; c < io * Jm; c += G) {
+        rh[c] = z;
+        rl[c] = z;
+      }
+      if (f == fe - 1)
+        for (int64_t c = (io + 1) * Jm + gl; c < ldY; c += G) {
+          rh[c] = z;
+          rl[c] = z;
+        }
+    }
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    float r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r[q] = 0.f;
+    for (int lb = 0; lb < maxlen; lb += G) {
+      const bool have = lb + gl < len;
+      const int my_idx = have ? leaf_idx[l0 + lb + gl] : 0;
+      const float my_val = have ? val[l0 + lb + gl] : 0.f;
+      const int cnt = min(G, maxlen - lb);
+#pragma unroll 4
+      for (int j = 0; j < cnt; ++j) {
+        const int idx = __shfl_sync(0xffffffffu, my_idx, j, G);
+        const float x = __shfl_sync(0xffffffffu, my_val, j, G);
+        if (lb + j < len) {
+          const float4* row = reinterpret_cast<const float4*>(Um + (int64_t)idx * ldm);
+          const float4 u0 = in0 ? row[gl] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 u1 = in1 ? row[gl + G] : make_float4(0.f, 0.f, 0.f, 0.f);
+          r[0] = fmaf(x, u0.x, r[0]); r[1] = fmaf(x, u0.y, r[1]);
+          r[2] = fmaf(x, u0.z, r[2]); r[3] = fmaf(x, u0.w, r[3]);
+          r[4] = fmaf(x, u1.x, r[4]); r[5] = fmaf(x, u1.y, r[5]);
+          r[6] = fmaf(x, u1.z, r[6]); r[7] = fmaf(x, u1.w, r[7]);
+        }
+      }
+    }
+    if (!active) continue;
+    const int64_t o = io * Jm;
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int c = 4 * (gl + G * v);
+#pragma unroll
+      for (int t = 0; t < 4; t += 2) {
+        if (c + t >= Jm) break;
+        const float y0 = r[4 * v + t], y1 = r[4 * v + t + 1];
+        if ((Jm & 1) == 0) {  // o + c + t even: a 4-byte BF16 pair
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(y0), h1 = __float2bfloat16_rn(y1);
+          __nv_bfloat162 hh, ll;
+          hh.x = h0;
+          hh.y = h1;
+          ll.x = __float2bfloat16_rn(y0 - __bfloat162float(h0));
+          ll.y = __float2bfloat16_rn(y1 - __bfloat162float(h1));
+          *reinterpret_cast<__nv_bfloat162*>(rh + o + c + t) = hh;
+          *reinterpret_cast<__nv_bfloat162*>(rl + o + c + t) = ll;
+        } else {
+          split_store(y0, rh, rl, o + c + t);
+          if (c + t + 1 < Jm) split_store(y1, rh, rl, o + c + t + 1);
+        }
+      }
+    }
+  }
+}
+
 template <int AP, int AQ>
-void launch_ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int Jm,
-                       const float* Uo, int Jo, __nv_bfloat16* Yh, __nv_bfloat16* Yl,
-                       int64_t ldY, float* Y32, cudaStream_t s) {
+void launch_ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um,
+                       int64_t ldm, int Jm, const float* Uo, int64_t ldo, int Jo,
+                       __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, float* Y32,
+                       cudaStream_t s) {
   dim3 grid((unsigned)X->dims[o->n], ceil_div(Jm, 16 * AP), ceil_div(Jo, 16 * AQ));
-  ttmc_mixed_kernel<AP, AQ><<<grid, 256, 0, s>>>(o->root_ptr, o->fiber_idx, o->fiber_ptr,
-                                                 o->leaf_idx, o->val_f32, Um, Jm, Uo, Jo, Yh, Yl,
-                                                 ldY, Y32);
+  const bool vec = AQ == 4 && ldo % 4 == 0 && (reinterpret_cast<uintptr_t>(Uo) & 15) == 0;
+  if (vec)
+    ttmc_mixed_kernel<AP, AQ, true><<<grid, 256, 0, s>>>(o->root_ptr, o->fiber_idx, o->fiber_ptr,
+                                                         o->leaf_idx, o->val_f32, Um, ldm, Jm, Uo,
+                                                         ldo, Jo, Yh, Yl, ldY, Y32);
+  else
+    ttmc_mixed_kernel<AP, AQ, false><<<grid, 256, 0, s>>>(o->root_ptr, o->fiber_idx,
+                                                          o->fiber_ptr, o->leaf_idx, o->val_f32,
+                                                          Um, ldm, Jm, Uo, ldo, Jo, Yh, Yl, ldY,
+                                                          Y32);
 }
 
 int tcode(int J) { return J <= 16 ? 1 : (J <= 32 ? 2 : 4); }
@@ -215,9 +401,9 @@ int ensure_val_f32(tucker_tensor_s* X, Ordering* ord, cudaStream_t s) {
   return f64_to_f32(ord->val, ord->val_f32, X->nnz, s);
 }
 
-int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int Jm,
-               const float* Uo, int Jo, __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY,
-               float* Y32, cudaStream_t s) {
+int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int64_t ldm, int Jm,
+               const float* Uo, int64_t ldo, int Jo, __nv_bfloat16* Yh, __nv_bfloat16* Yl,
+               int64_t ldY, float* Y32, cudaStream_t s) {
   if (X->dims[o->n] == 0) return TUCKER_OK;
   const double nnz = (double)X->nnz, F = (double)o->F;
   ProfScope prof("ttmc_mixed", s, 2.0 * (nnz * Jo + F * Jm * Jo),
@@ -226,7 +412,8 @@ int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int
                      4.0 * (X->dims[o->m] * (double)Jm + X->dims[o->o] * (double)Jo));
   const int cp = tcode(Jm), cq = tcode(Jo);
 #define TK_TM(A, B) \
-  if (cp == A && cq == B) launch_ttmc_mixed<A, B>(X, o, Um, Jm, Uo, Jo, Yh, Yl, ldY, Y32, s);
+  if (cp == A && cq == B)                                                                    \
+    launch_ttmc_mixed<A, B>(X, o, Um, ldm, Jm, Uo, ldo, Jo, Yh, Yl, ldY, Y32, s);
   TK_TM(1, 1) TK_TM(1, 2) TK_TM(1, 4) TK_TM(2, 1) TK_TM(2, 2) TK_TM(2, 4) TK_TM(4, 1)
   TK_TM(4, 2) TK_TM(4, 4)
 #undef TK_TM
@@ -234,23 +421,44 @@ int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int
   return TUCKER_OK;
 }
 
-int slice_proj_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int Jm,
-                     __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, cudaStream_t s) {
+int slice_proj_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int64_t ldm,
+                     int Jm, __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, cudaStream_t s) {
   // ordering (n, o, m): fibers (i_n, i_o), leaves i_m.
   const int64_t In = X->dims[o->n], Io = X->dims[o->m];
   if (In == 0) return TUCKER_OK;
   ProfScope prof("slice_proj_mixed", s, 2.0 * (double)X->nnz * Jm,
                  8.0 * X->nnz + 16.0 * o->F + 4.0 * (double)In * Io * Jm +
                      4.0 * X->dims[o->o] * (double)Jm);
+  const bool vec = ldm % 4 == 0 && (reinterpret_cast<uintptr_t>(Um) & 15) == 0 && Jm <= 128;
+  if (vec) {
+    if (Jm <= 64)
+      slice_proj_mixed_vec_kernel<8><<<(unsigned)In, 256, 0, s>>>(
+          o->root_ptr, o->fiber_idx, o->fiber_ptr, o->leaf_idx, o->val_f32, Um, ldm, Jm, Yh, Yl,
+          ldY);
+    else
+      slice_proj_mixed_vec_kernel<16><<<(unsigned)In, 256, 0, s>>>(
+          o->root_ptr, o->fiber_idx, o->fiber_ptr, o->leaf_idx, o->val_f32, Um, ldm, Jm, Yh, Yl,
+          ldY);
+    TK_LAUNCH();
+    return TUCKER_OK;
+  }
   const int np = Jm <= 32 ? 1 : (Jm <= 64 ? 2 : (Jm <= 128 ? 4 : 8));
-#define TK_SPM(N)                                                                           \
-  if (np == N)                                                                              \
-    slice_proj_mixed_kernel<N><<<(unsigned)In, 256, 0, s>>>(o->root_ptr, o->fiber_idx,      \
-                                                            o->fiber_ptr, o->leaf_idx,      \
-                                                            o->val_f32, Um, Jm, Io, Yh, Yl, \
+#define TK_SPM(N)                                                                             \
+  if (np == N)                                                                                \
+    slice_proj_mixed_kernel<N><<<(unsigned)In, 256, 0, s>>>(o->root_ptr, o->fiber_idx,        \
+                                                            o->fiber_ptr, o->leaf_idx,        \
+                                                            o->val_f32, Um, ldm, Jm, Yh, Yl,  \
                                                             ldY);
   TK_SPM(1) TK_SPM(2) TK_SPM(4) TK_SPM(8)
 #undef TK_SPM
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+int f64_to_f32_rows(const double* a, int64_t rows, int cols, float* b, int64_t ldb,
+                    cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return TUCKER_OK;
+  f64_to_f32_rows_kernel<<<ceil_div(rows * ldb, 256), 256, 0, s>>>(a, rows, cols, b, ldb);
   TK_LAUNCH();
   return TUCKER_OK;
 }

@@ -53,7 +53,7 @@ def ragged(tucker_lib):
     return X, tucker_lib.tucker_tensor_create(X.idx, X.val, X.dims)
 
 
-@pytest.mark.parametrize("J", [(5, 17, 33), (70, 9, 40)])
+@pytest.mark.parametrize("J", [(5, 17, 33), (70, 9, 40), (12, 48, 64)])   # scalar and float4 rows
 def test_ttmc_mixed(tucker_lib, ragged, J):
     X, T = ragged
     U = [(synth.uniform_matrix(X.dims[a], J[a], 200 + a) - 0.5).astype(np.float32)
@@ -70,7 +70,7 @@ def test_ttmc_mixed(tucker_lib, ragged, J):
         assert not H[:, K:].any() and not L[:, K:].any()
 
 
-@pytest.mark.parametrize("Jm", [3, 40, 130])
+@pytest.mark.parametrize("Jm", [3, 40, 64, 100, 130])   # scalar and float4 row paths
 def test_slice_proj_mixed(tucker_lib, ragged, Jm):
     X, T = ragged
     for n, m in [(0, 2), (1, 0), (2, 1), (0, 1)]:
