@@ -945,6 +945,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     TK_LAUNCH();
     TK_CUDA(cudaMemcpyAsync(th.data(), evh.p, sizeof(double) * ka, cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaMemcpyAsync(rr.data(), rn.p, sizeof(double) * ka, cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
     theta1 = std::max(theta1, th[0]);
     const double thr = tol * std::max(theta1, 1e-300);
     int nlock = 0;
