@@ -206,7 +206,7 @@ COUNTERS = ("eig_outer", "syev_steps", "syev_fp32_sweeps", "syev_fallback")   # 
 # algorithmic bytes: the traffic of both kernels grows with the rows x K of the projection read.
 NCU_TRAFFIC_RATIO = {
     "syrk_f64": 10.034e6 / (8.0 * 500 * 2500 + 8.0 * 500 * 500),
-    "gram_bf16x3": 178.65e6 / (4.0 * 500 * 50000 + 8.0 * 500 * 500),
+    "gram_bf16x3": 105.01e6 / (4.0 * 500 * 50000 + 8.0 * 500 * 500),
 }
 
 

@@ -275,7 +275,7 @@ gram_bf16x3_kernel(const __grid_constant__ TermMaps maps, const Job* __restrict_
 // order, in FP64; mirrored to M[c][r].
 __global__ void gram_reduce_kernel(const float* __restrict__ partial,
                                    const int* __restrict__ pair_first,
-                                   const int* __restrict__ pair_count, int ntiles, int rows,
+                                   const int* __restrict__ pair_count, int stride, int rows,
                                    double* __restrict__ M) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)rows * rows) return;
@@ -286,7 +286,8 @@ __global__ void gram_reduce_kernel(const float* __restrict__ partial,
   const int rr = r - ti * TM, cc = c - tj * TM;
   double s = 0.0;
   const int j0 = pair_first[pr], nj = pair_count[pr];
-  for (int j = 0; j < nj; ++j) s += (double)partial[(int64_t)(j0 + j) * TM * TM + rr * TM + cc];
+  for (int j = 0; j < nj; ++j)
+    s += (double)partial[((int64_t)j0 + (int64_t)j * stride) * TM * TM + rr * TM + cc];
   M[(int64_t)r * rows + c] = s;
   M[(int64_t)c * rows + r] = s;
 }
@@ -347,18 +348,24 @@ int gram_bf16x3(int rows, int nterms, const GramTerm* terms, double* M, cudaStre
   chunk = (chunk + TK - 1) / TK * TK;
   if (chunk < 4 * TK) chunk = 4 * TK;
   if (chunk > KCHUNK_MAX) chunk = KCHUNK_MAX;
+  // Jobs in chunk-major order: the CTAs that run together work on the same K range of every
+  // tile pair, so each row tile's chunk comes from DRAM once and is re-read from L2 by the
+  // other pairs (a 1000-row chunk of hi + lo is 16 MB).  Job c * npairs + pr is chunk c of
+  // pair pr; the reduction adds a pair's chunks in chunk order.
   std::vector<Job> jobs;
   std::vector<int> first(npairs), count(npairs);
-  for (int ti = 0, pr = 0; ti < nt; ++ti)
-    for (int tj = 0; tj <= ti; ++tj, ++pr) {
-      first[pr] = (int)jobs.size();
-      for (int t = 0; t < nterms; ++t)
-        for (int64_t k0 = 0; k0 < terms[t].K; k0 += chunk) {
-          const int64_t k1 = std::min<int64_t>(terms[t].K, k0 + chunk);
+  int nchunks = 0;
+  for (int t = 0; t < nterms; ++t)
+    for (int64_t k0 = 0; k0 < terms[t].K; k0 += chunk, ++nchunks) {
+      const int64_t k1 = std::min<int64_t>(terms[t].K, k0 + chunk);
+      for (int ti = 0; ti < nt; ++ti)
+        for (int tj = 0; tj <= ti; ++tj)
           jobs.push_back(Job{ti, tj, t, (int)k0, (int)((k1 - k0 + TK - 1) / TK)});
-        }
-      count[pr] = (int)jobs.size() - first[pr];
     }
+  for (int pr = 0; pr < npairs; ++pr) {
+    first[pr] = pr;
+    count[pr] = nchunks;
+  }
   const int64_t njobs = (int64_t)jobs.size();
   const double flops = 2.0 * 3.0 * (double)Ktot * TM * TM * npairs;
   ProfScope prof("gram_bf16x3", s, (double)rows * (rows + 1) * (double)Ktot,
@@ -381,7 +388,7 @@ int gram_bf16x3(int rows, int nterms, const GramTerm* terms, double* M, cudaStre
                                                                part.as<float>(), st.as<int>());
   TK_LAUNCH();
   gram_reduce_kernel<<<ceil_div((int64_t)rows * rows, 256), 256, 0, s>>>(
-      part.as<float>(), dfirst.as<int>(), dcount.as<int>(), nt, rows, M);
+      part.as<float>(), dfirst.as<int>(), dcount.as<int>(), npairs, rows, M);
   TK_LAUNCH();
   int h = 0;
   TK_CUDA(cudaMemcpyAsync(&h, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
