@@ -849,7 +849,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   bool use32 = M32 != nullptr;
   const int max_outer = 120, dmax = 24;
   const double growth_cap = 1e4, abs_cap = 1e8;
-  Buf Vb, T1, T2, T3, H, Qh, evh, Gk, R, Ri, rd, Tc, P, rn, stat;
+  Buf Vb, T1, T2, T3, H, Qh, evrn, Gk, R, Ri, rd, Tc, P, stat;
   Buf Md, Md32, LS, Lt, lamd;  // deflated filter operator and its factors
   TK_TRY(Md.alloc(sizeof(double) * n * n, s));
   if (M32) TK_TRY(Md32.alloc(sizeof(float) * n * n, s));
@@ -865,7 +865,9 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   TK_TRY(T3.alloc(nk, s));
   TK_TRY(H.alloc(sizeof(double) * k * k, s));
   TK_TRY(Qh.alloc(sizeof(double) * k * k, s));
-  TK_TRY(evh.alloc(sizeof(double) * k, s));
+  TK_TRY(evrn.alloc(sizeof(double) * 2 * k, s));  // Ritz values [k], residual norms [k]
+  double* evh = evrn.as<double>();
+  double* rn = evh + k;
   TK_TRY(Gk.alloc(sizeof(double) * k * k, s));
   TK_TRY(R.alloc(sizeof(double) * k * k, s));
   TK_TRY(rd.alloc(sizeof(double) * k, s));
@@ -874,7 +876,6 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     TK_TRY(Tc.alloc(nk, s));
   }
   TK_TRY(P.alloc(sizeof(double) * k * k, s));
-  TK_TRY(rn.alloc(sizeof(double) * k, s));
   TK_TRY(stat.alloc(sizeof(int) * 8, s));
   const CholWork cw{Tc.as<double>(), Gk.as<double>(), R.as<double>(), Ri.as<double>(),
                     rd.as<double>(), stat.as<int>()};
@@ -915,7 +916,9 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   int nl = 0;
   double theta1 = 0.0;
   std::vector<double> locked_theta;
-  std::vector<double> th(k), rr(k);
+  std::vector<double> thrr(2 * (size_t)k);
+  double* th = thrr.data();
+  double* rr = th + k;
   bool done = false;
   for (int outer = 0; outer < max_outer; ++outer) {
     st->outer_iters = outer + 1;
@@ -929,7 +932,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     // Eigenpairs of H to a tenth of the locking tolerance (relative to the largest Ritz value
     // seen so far, or to |H| on the first solve).
     SyevStats ss;
-    const int js = syev_refined(H.as<double>(), ka, ka, Qh.as<double>(), evh.as<double>(),
+    const int js = syev_refined(H.as<double>(), ka, ka, Qh.as<double>(), evh,
                                 theta1, 0.1 * tol, s, &ss);
     st->jacobi_sweeps += ss.fp32_sweeps + ss.fp64_sweeps;
     st->refine_steps += ss.steps;
@@ -940,11 +943,10 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     TK_TRY(gemm_nn_f64(n, ka, ka, 1.0, W, ka, Qh.as<double>(), ka, 0.0, nullptr, 0, 0.0, nullptr,
                        0, T3.as<double>(), ka, s));
     TK_TRY(copy_cols_f64(n, ka, T2.as<double>(), ka, Va, k, s));
-    residual_norms<<<ka, 256, 0, s>>>(T3.as<double>(), T2.as<double>(), ka, n, evh.as<double>(),
-                                      rn.as<double>());
+    residual_norms<<<ka, 256, 0, s>>>(T3.as<double>(), T2.as<double>(), ka, n, evh, rn);
     TK_LAUNCH();
-    TK_CUDA(cudaMemcpyAsync(th.data(), evh.p, sizeof(double) * ka, cudaMemcpyDeviceToHost, s));
-    TK_CUDA(cudaMemcpyAsync(rr.data(), rn.p, sizeof(double) * ka, cudaMemcpyDeviceToHost, s));
+    // one copy of both (Ritz values in [0, k), residuals in [k, 2k))
+    TK_CUDA(cudaMemcpyAsync(thrr.data(), evh, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
     theta1 = std::max(theta1, th[0]);
     const double thr = tol * std::max(theta1, 1e-300);
@@ -974,7 +976,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     }
     // Chebyshev filter on the remaining active columns.
     const int ka2 = k - nl;
-    const double* tha = th.data() + nlock;
+    const double* tha = th + nlock;
     // Unwanted interval [0, b]; when M has fewer than k nonzero eigenvalues the smallest Ritz
     // value is ~0, so b is floored to keep the map (x - c) / e finite.
     const double b = std::max(tha[ka2 - 1], 1e-10 * theta1);

@@ -20,6 +20,7 @@
 //      cluster that the first-order step cannot split (and that would matter at the caller's
 //      tolerance) sends the problem to the FP64 Jacobi instead.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -310,14 +311,17 @@ int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* eval
   ProfScope prof("syev_refined", s, 0.0, 0.0);
   const int mp = m + (m & 1);
   const int64_t ld = 2 * (int64_t)m;  // [W | X] and [S | G] side by side
-  Buf WX0, WX1, SG, E, lam, stats, info;
+  // misc: per-column statistics [3m], lambda [m], the FP32 Jacobi's info [2 ints]: one
+  // device-to-host copy reads all of them.
+  Buf WX0, WX1, SG, E, misc;
   TK_TRY(WX0.alloc(sizeof(double) * m * ld, s));
   TK_TRY(WX1.alloc(sizeof(double) * m * ld, s));
   TK_TRY(SG.alloc(sizeof(double) * m * ld, s));
   TK_TRY(E.alloc(sizeof(double) * m * m, s));
-  TK_TRY(lam.alloc(sizeof(double) * m, s));
-  TK_TRY(stats.alloc(sizeof(double) * 3 * m, s));
-  TK_TRY(info.alloc(sizeof(int) * 2, s));
+  TK_TRY(misc.alloc(sizeof(double) * (4 * (size_t)m + 1), s));
+  double* stats = misc.as<double>();
+  double* lam = stats + 3 * m;
+  int* info = reinterpret_cast<int*>(lam + m);
   double* cur = WX0.as<double>();
   double* nxt = WX1.as<double>();
   {
@@ -328,36 +332,35 @@ int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* eval
     TK_CUDA(attr);
     {
       ProfScope pj("syev_jacobi32", s, 0.0, 0.0);
-      jacobi32_kernel<<<1, 1024, smem, s>>>(A, m, lda, 1e-6f, 1e-7f, 40, cur + m, ld,
-                                            info.as<int>());
+      jacobi32_kernel<<<1, 1024, smem, s>>>(A, m, lda, 1e-6f, 1e-7f, 40, cur + m, ld, info);
     }
     TK_LAUNCH();
   }
   // Refinement.  The statistics are read back (one host synchronisation each) from the step
-  // `first_check` on: from an FP32 start the first two steps never meet the orthogonality bar.
+  // `first_check` on: from an FP32 start two steps rarely, and three steps usually, meet the
+  // bars, so checking from step 3 needs one synchronisation in the common case.
   const int max_steps = 6;
-  const int first_check = 2;
+  const int first_check = 3;
   const double bad_rel = acc_rel;
-  std::vector<double> hs(3 * (size_t)m);
+  std::vector<double> hs(4 * (size_t)m + 1);
+  int hinfo[2] = {0, 0};
   bool accepted = false, cluster = false;
   int step = 0;
   for (; step <= max_steps; ++step) {
     double* X = cur + m;
     TK_TRY(gemm_nn_f64(m, m, m, 1.0, A, lda, X, ld, 0.0, nullptr, 0, 0.0, nullptr, 0, cur, ld, s));
     TK_TRY(gemm_tn_f64(m, 2 * m, m, X, ld, cur, ld, SG.as<double>(), ld, s));
-    oa_lambda_kernel<<<ceil_div(m, 128), 128, 0, s>>>(SG.as<double>(), m, ld, lam.as<double>());
+    oa_lambda_kernel<<<ceil_div(m, 128), 128, 0, s>>>(SG.as<double>(), m, ld, lam);
     TK_LAUNCH();
-    oa_column_kernel<<<m, 256, 0, s>>>(SG.as<double>(), m, ld, lam.as<double>(), scale, bad_rel,
-                                       E.as<double>(), stats.as<double>());
+    oa_column_kernel<<<m, 256, 0, s>>>(SG.as<double>(), m, ld, lam, scale, bad_rel,
+                                       E.as<double>(), stats);
     TK_LAUNCH();
     if (step >= first_check) {
-      TK_CUDA(cudaMemcpyAsync(hs.data(), stats.p, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost,
-                              s));
-      double hl_max = 0.0;
-      std::vector<double> hl(m);
-      TK_CUDA(cudaMemcpyAsync(hl.data(), lam.p, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+      TK_CUDA(cudaMemcpyAsync(hs.data(), misc.p, misc.bytes, cudaMemcpyDeviceToHost, s));
       TK_CUDA(cudaStreamSynchronize(s));
-      for (double v : hl) hl_max = std::max(hl_max, fabs(v));
+      memcpy(hinfo, hs.data() + 4 * m, sizeof(hinfo));
+      double hl_max = 0.0;
+      for (int j = 0; j < m; ++j) hl_max = std::max(hl_max, fabs(hs[3 * m + j]));
       const double thr = acc_rel * std::max(hl_max, scale);
       double off = 0.0, orth = 0.0, bad = 0.0;
       for (int j = 0; j < m; ++j) {
@@ -384,9 +387,6 @@ int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* eval
     std::swap(cur, nxt);
   }
   st->steps = step;
-  int hinfo[2] = {0, 0};
-  TK_CUDA(cudaMemcpyAsync(hinfo, info.p, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
-  TK_CUDA(cudaStreamSynchronize(s));
   st->fp32_sweeps = hinfo[0];
   prof_count("syev_fp32_sweeps", (double)hinfo[0]);
   prof_count("syev_steps", (double)step);
@@ -395,7 +395,7 @@ int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* eval
     prof_count("syev_fallback", cluster ? 1.0 : 2.0);
     return jacobi_eig(A, m, lda, Qout, evals_out, s, &st->fp64_sweeps);
   }
-  return sort_eig_desc(cur + m, ld, m, lam.as<double>(), Qout, m, evals_out, s);
+  return sort_eig_desc(cur + m, ld, m, lam, Qout, m, evals_out, s);
 }
 
 }  // namespace tk
