@@ -445,7 +445,7 @@ chol_kernel(const double* __restrict__ G, int k, int64_t nrows, double* __restri
 // RW independent substitution chains are interleaved to hide their latency.  Skipped when the
 // factorisation that made R broke down.
 template <int KT, int RW>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(64)
 trsm_rows_kernel(double* __restrict__ V, int64_t ldv, int n, int k, const double* __restrict__ R,
                  const double* __restrict__ rdinv, const int* __restrict__ status) {
   if (*status & DEV_CHOL_BREAKDOWN) return;
@@ -497,11 +497,13 @@ trsm_rows_kernel(double* __restrict__ V, int64_t ldv, int n, int k, const double
   }
 }
 
+// One row per warp, two warps per CTA: every row is a serial chain of k FP64 steps, and FP64
+// issue is per SM sub-partition, so the rows are spread over as many sub-partitions as possible
+// (8-warp CTAs left most of the SMs idle for n of a few hundred).
 template <int KT>
 void launch_trsm(double* V, int64_t ldv, int n, int k, const double* R, const double* rdinv,
                  const int* status, cudaStream_t s) {
-  constexpr int RW = KT <= 6 ? 2 : 1;
-  trsm_rows_kernel<KT, RW><<<ceil_div(n, 8 * RW), 256, 0, s>>>(V, ldv, n, k, R, rdinv, status);
+  trsm_rows_kernel<KT, 1><<<ceil_div(n, 2), 64, 0, s>>>(V, ldv, n, k, R, rdinv, status);
 }
 
 int trsm_rows(double* V, int64_t ldv, int n, int k, const double* R, const double* rdinv,
