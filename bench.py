@@ -328,6 +328,8 @@ def batched_leg(args):
                       "value": passes / wall, "unit": "tensor-sweeps/s",
                       "ms_per_step": 1e3 * wall / args.steps, "steps": args.steps,
                       "warmup": args.warmup, "precision": "mixed",
+                      "autotune": [tk.tucker_autotune_decision(i)
+                                   for i in range(tk.tucker_autotune_count())],
                       "fp64_one_at_a_time": {"value": ns * 2 * SWEEPS / single,
                                              "unit": "tensor-sweeps/s",
                                              "sample": f"first {ns} tensors, HOOI + MP"},

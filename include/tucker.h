@@ -214,6 +214,22 @@ int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const dou
  * iterations of one solve).  Every name and the argument order are fixed; unknown names
  * report zero.  tucker_launch_count returns the number of kernels this library has launched
  * in the process. */
+/* ---- autotuning (no counterpart in the paper) -------------------------------------------
+ * The mixed-precision projections have two kernels each that compute the same result up to the
+ * order of FP32 sums: variant 0 gives each fiber a group of 8 lanes that loads factor rows as
+ * float4 (rows padded to 16 bytes), variant 1 gives each fiber a warp.  On the first call for a
+ * shape class (family; core sizes; rounded log2 of the mean fiber length) the library times both
+ * once on the caller's stream and keeps the faster for the rest of the process, so every later
+ * call, single-tensor or batched, runs the same kernel.  tucker_autotune_enable(0) stops new
+ * timing (classes without a decision then use variant 0).  tucker_autotune_count returns the
+ * number of decisions; tucker_autotune_decision reads decision i (0-based): family (1 HOOI
+ * projection, 2 SP/MP slice projection), key[3] (J_m, J_o or 0, fiber-length class), the kept
+ * variant and both measured times in milliseconds (kept first); EINVAL for i out of range. */
+void tucker_autotune_enable(int on);
+int tucker_autotune_count(void);
+int tucker_autotune_decision(int32_t i, int32_t* family, int32_t key[3], int32_t* variant,
+                             double* ms_kept, double* ms_other);
+
 void tucker_profile_enable(int on);
 int tucker_profile_query(const char* name, int64_t* launches, double* total_ms, double* flops,
                          double* bytes);

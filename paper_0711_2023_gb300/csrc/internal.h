@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace tk {
@@ -120,6 +122,13 @@ int jacobi_eig(const double* A, int m, int64_t lda, double* Qout, double* evals_
 // Columns of Q (m x m, ld ldq) reordered by descending ev into Qout (ld ldo), ev into evals_out.
 int sort_eig_desc(const double* Q, int64_t ldq, int m, const double* ev, double* Qout,
                   int64_t ldo, double* evals_out, cudaStream_t s);
+
+// autotune.cu: runs run(v) for the variant v kept for the shape class (family, a, b, c); on the
+// class's first call (while tuning is enabled) times variants 0 and 1 once each on s, keeps the
+// faster and runs it again.  With tuning disabled and no decision yet, runs variant 0.
+enum { TUNE_TTMC_MIXED = 1, TUNE_SLICE_MIXED = 2 };
+int autotune_run(int family, int a, int b, int c, const std::function<int(int)>& run,
+                 cudaStream_t s);
 
 // syev.cu: the same contract as jacobi_eig, solved in FP32 and refined in FP64 until every
 // column's off-diagonal mass of X^T A X is below acc_rel * max(|A|_2, scale) and X is

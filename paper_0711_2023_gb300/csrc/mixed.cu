@@ -7,6 +7,9 @@
 // reads with TMA.  HOOI's projection can also be written in FP32 for the core.
 // As in the FP64 kernels, every output element has one writer and a fixed summation order.
 #include <cuda_bf16.h>
+#include <math.h>
+
+#include <functional>
 
 #include "internal.h"
 
@@ -362,10 +365,9 @@ slice_proj_mixed_vec_kernel(const int64_t* __restrict__ root_ptr,
 template <int AP, int AQ>
 void launch_ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um,
                        int64_t ldm, int Jm, const float* Uo, int64_t ldo, int Jo,
-                       __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, float* Y32,
+                       __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, float* Y32, bool vec,
                        cudaStream_t s) {
   dim3 grid((unsigned)X->dims[o->n], ceil_div(Jm, 16 * AP), ceil_div(Jo, 16 * AQ));
-  const bool vec = AQ == 4 && ldo % 4 == 0 && (reinterpret_cast<uintptr_t>(Uo) & 15) == 0;
   if (vec)
     ttmc_mixed_kernel<AP, AQ, true><<<grid, 256, 0, s>>>(o->root_ptr, o->fiber_idx, o->fiber_ptr,
                                                          o->leaf_idx, o->val_f32, Um, ldm, Jm, Uo,
@@ -378,6 +380,17 @@ void launch_ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float*
 }
 
 int tcode(int J) { return J <= 16 ? 1 : (J <= 32 ? 2 : 4); }
+
+// Shape class of a projection for the autotuner: round(log2(mean fiber length)).
+int fiber_class(int64_t nnz, int64_t F) {
+  if (F <= 0 || nnz <= F) return 0;
+  const int c = (int)lround(log2((double)nnz / (double)F));
+  return c < 0 ? 0 : (c > 16 ? 16 : c);
+}
+
+bool rows16(const float* U, int64_t ld) {
+  return ld % 4 == 0 && (reinterpret_cast<uintptr_t>(U) & 15) == 0;
+}
 
 }  // namespace
 
@@ -411,14 +424,22 @@ int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int
                      (Y32 ? 4.0 : 0.0) * X->dims[o->n] * (double)Jm * Jo +
                      4.0 * (X->dims[o->m] * (double)Jm + X->dims[o->o] * (double)Jo));
   const int cp = tcode(Jm), cq = tcode(Jo);
-#define TK_TM(A, B) \
-  if (cp == A && cq == B)                                                                    \
-    launch_ttmc_mixed<A, B>(X, o, Um, ldm, Jm, Uo, ldo, Jo, Yh, Yl, ldY, Y32, s);
-  TK_TM(1, 1) TK_TM(1, 2) TK_TM(1, 4) TK_TM(2, 1) TK_TM(2, 2) TK_TM(2, 4) TK_TM(4, 1)
-  TK_TM(4, 2) TK_TM(4, 4)
+  // Variant 0: the leaf phase with lane groups and float4 rows of U_o (64-column tiles, rows
+  // padded to 16 bytes); variant 1: one warp per fiber.  The autotuner picks per shape class.
+  const bool vec_ok = cq == 4 && rows16(Uo, ldo);
+  auto run = [&](int variant) -> int {
+    const bool vec = vec_ok && variant == 0;
+#define TK_TM(A, B)                                                                  \
+  if (cp == A && cq == B)                                                            \
+    launch_ttmc_mixed<A, B>(X, o, Um, ldm, Jm, Uo, ldo, Jo, Yh, Yl, ldY, Y32, vec, s);
+    TK_TM(1, 1) TK_TM(1, 2) TK_TM(1, 4) TK_TM(2, 1) TK_TM(2, 2) TK_TM(2, 4) TK_TM(4, 1)
+    TK_TM(4, 2) TK_TM(4, 4)
 #undef TK_TM
-  TK_LAUNCH();
-  return TUCKER_OK;
+    TK_LAUNCH();
+    return TUCKER_OK;
+  };
+  if (!vec_ok) return run(1);
+  return autotune_run(TUNE_TTMC_MIXED, Jm, Jo, fiber_class(X->nnz, o->F), run, s);
 }
 
 int slice_proj_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int64_t ldm,
@@ -429,30 +450,36 @@ int slice_proj_mixed(const tucker_tensor_s* X, const Ordering* o, const float* U
   ProfScope prof("slice_proj_mixed", s, 2.0 * (double)X->nnz * Jm,
                  8.0 * X->nnz + 16.0 * o->F + 4.0 * (double)In * Io * Jm +
                      4.0 * X->dims[o->o] * (double)Jm);
-  const bool vec = ldm % 4 == 0 && (reinterpret_cast<uintptr_t>(Um) & 15) == 0 && Jm <= 128;
-  if (vec) {
-    if (Jm <= 64)
-      slice_proj_mixed_vec_kernel<8><<<(unsigned)In, 256, 0, s>>>(
-          o->root_ptr, o->fiber_idx, o->fiber_ptr, o->leaf_idx, o->val_f32, Um, ldm, Jm, Yh, Yl,
-          ldY);
-    else
-      slice_proj_mixed_vec_kernel<16><<<(unsigned)In, 256, 0, s>>>(
-          o->root_ptr, o->fiber_idx, o->fiber_ptr, o->leaf_idx, o->val_f32, Um, ldm, Jm, Yh, Yl,
-          ldY);
+  // Variant 0: a lane group per fiber with float4 rows of U_m (J_m <= 128, rows padded to 16
+  // bytes); variant 1: one warp per fiber.  The autotuner picks per shape class.
+  const bool vec_ok = rows16(Um, ldm) && Jm <= 128;
+  auto run = [&](int variant) -> int {
+    if (vec_ok && variant == 0) {
+      if (Jm <= 64)
+        slice_proj_mixed_vec_kernel<8><<<(unsigned)In, 256, 0, s>>>(
+            o->root_ptr, o->fiber_idx, o->fiber_ptr, o->leaf_idx, o->val_f32, Um, ldm, Jm, Yh,
+            Yl, ldY);
+      else
+        slice_proj_mixed_vec_kernel<16><<<(unsigned)In, 256, 0, s>>>(
+            o->root_ptr, o->fiber_idx, o->fiber_ptr, o->leaf_idx, o->val_f32, Um, ldm, Jm, Yh,
+            Yl, ldY);
+      TK_LAUNCH();
+      return TUCKER_OK;
+    }
+    const int np = Jm <= 32 ? 1 : (Jm <= 64 ? 2 : (Jm <= 128 ? 4 : 8));
+#define TK_SPM(N)                                                                           \
+  if (np == N)                                                                              \
+    slice_proj_mixed_kernel<N><<<(unsigned)In, 256, 0, s>>>(o->root_ptr, o->fiber_idx,      \
+                                                            o->fiber_ptr, o->leaf_idx,      \
+                                                            o->val_f32, Um, ldm, Jm, Yh, Yl, \
+                                                            ldY);
+    TK_SPM(1) TK_SPM(2) TK_SPM(4) TK_SPM(8)
+#undef TK_SPM
     TK_LAUNCH();
     return TUCKER_OK;
-  }
-  const int np = Jm <= 32 ? 1 : (Jm <= 64 ? 2 : (Jm <= 128 ? 4 : 8));
-#define TK_SPM(N)                                                                             \
-  if (np == N)                                                                                \
-    slice_proj_mixed_kernel<N><<<(unsigned)In, 256, 0, s>>>(o->root_ptr, o->fiber_idx,        \
-                                                            o->fiber_ptr, o->leaf_idx,        \
-                                                            o->val_f32, Um, ldm, Jm, Yh, Yl,  \
-                                                            ldY);
-  TK_SPM(1) TK_SPM(2) TK_SPM(4) TK_SPM(8)
-#undef TK_SPM
-  TK_LAUNCH();
-  return TUCKER_OK;
+  };
+  if (!vec_ok) return run(1);
+  return autotune_run(TUNE_SLICE_MIXED, Jm, 0, fiber_class(X->nnz, o->F), run, s);
 }
 
 int f64_to_f32_rows(const double* a, int64_t rows, int cols, float* b, int64_t ldb,

@@ -1,6 +1,7 @@
 // Opt-in kernel timing: CUDA events recorded on the launching stream around the hot-path
 // kernels, with each launch's algorithmic FLOPs and bytes, named counters of the iterative
-// parts (values summed), plus a count of every kernel launch the library makes.  Used by the benchmark to report achieved rates against the roofline.
+// parts (values summed), plus a count of every kernel launch the library makes.  Used by the
+// benchmark to report achieved rates against the roofline.
 #include <atomic>
 #include <mutex>
 #include <string.h>

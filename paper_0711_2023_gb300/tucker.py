@@ -90,6 +90,10 @@ _SIGS = {
     "tucker_profile_query": (c_int32, [c_char_p, POINTER(c_int64), POINTER(c_double),
                                        POINTER(c_double), POINTER(c_double)]),
     "tucker_launch_count": (c_int64, []),
+    "tucker_autotune_enable": (None, [c_int32]),
+    "tucker_autotune_count": (c_int32, []),
+    "tucker_autotune_decision": (c_int32, [c_int32, POINTER(c_int32), POINTER(c_int32),
+                                           POINTER(c_int32), POINTER(c_double), POINTER(c_double)]),
 }
 
 
@@ -496,6 +500,26 @@ def tucker_profile_query(name: str):
 
 def tucker_launch_count() -> int:
     return int(_lib().tucker_launch_count())
+
+
+def tucker_autotune_enable(on: bool):
+    _lib().tucker_autotune_enable(1 if on else 0)
+
+
+def tucker_autotune_count() -> int:
+    return int(_lib().tucker_autotune_count())
+
+
+def tucker_autotune_decision(i: int):
+    """Decision i of the kernel-variant autotuner: dict(family, key, variant, ms_kept, ms_other)."""
+    fam, var = c_int32(), c_int32()
+    key = (c_int32 * 3)()
+    a, b = c_double(), c_double()
+    _check(_lib().tucker_autotune_decision(int(i), ctypes.byref(fam), key, ctypes.byref(var),
+                                           ctypes.byref(a), ctypes.byref(b)),
+           "tucker_autotune_decision")
+    return dict(family=int(fam.value), key=tuple(int(k) for k in key), variant=int(var.value),
+                ms_kept=float(a.value), ms_other=float(b.value))
 
 
 def header_functions(header_path=None):

@@ -122,6 +122,30 @@ def test_eig_topk(tucker_lib, n, J):
     assert np.abs(U - V).max() <= 1e-8
 
 
+@pytest.mark.parametrize("n", [120, 400])   # all-eigenpairs path and subspace path
+def test_eig_topk_clusters_and_outlier(tucker_lib, n):
+    """Spectra the small eigensolver's first-order refinement cannot split on its own: an exact
+    triple, a pair 1e-9 apart, a pair 1e-6 apart (these go to the FP64 Jacobi fallback when they
+    matter at the tolerance), under an outlier 1e4 times the bulk, with a clear gap after J."""
+    J = 24
+    Q, _ = np.linalg.qr(synth.uniform_matrix(n, n, 900 + n) - 0.5)
+    w = np.concatenate([[1e4], [7.0, 7.0, 7.0], [5.0, 5.0 + 5e-9], [3.0, 3.0 + 3e-6],
+                        np.linspace(2.5, 1.0, J - 8), 0.1 * np.linspace(1.0, 0.0, n - J)])
+    M = (Q * w) @ Q.T
+    M = 0.5 * (M + M.T)
+    U, lam = tucker_lib.tucker_eig_topk(M, J)
+    U, lam = U.cpu().numpy(), lam.cpu().numpy()
+    V, wr = O.leading_eigvecs(M, J)
+    np.testing.assert_allclose(lam, wr[:J], rtol=1e-11, atol=1e-12 * wr[0])
+    # The J-subspace is well posed (gap 0.9 after J).  The subspace path locks at residual
+    # 3e-13 * theta_1 = 3e-9 here, so by Davis-Kahan sin(angle) <= 3e-9 / 0.9.
+    assert O.subspace_distance(U, V) <= 1e-8
+    assert np.abs(U.T @ U - np.eye(J)).max() <= 1e-12
+    # within a cluster any orthonormal basis is right: check each column is an eigenvector
+    res = np.linalg.norm(M @ U - U * lam, axis=0)
+    assert res.max() <= 1e-11 * wr[0]
+
+
 def test_eig_topk_warm_start_and_uniform_tensor_gram(tucker_lib):
     X = synth.random_sparse_tensor((300, 280, 260), 200000, 601)
     M = O.unfolding_gram(X.dims, X.idx, X.val, 0)
