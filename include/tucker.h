@@ -188,8 +188,12 @@ int tucker_gram_bf16x3(const uint16_t* d_Y1hi, const uint16_t* d_Y1lo, int64_t K
 /* J leading eigenvectors of the symmetric positive semi-definite n x n matrix M (largest
  * eigenvalue first; in each column the entry of largest magnitude is positive).  d_U0
  * (n x J, may be NULL) is a starting guess.  Outputs d_U (n x J) and d_lambda (J).
- * Block subspace iteration with Chebyshev filtering, Cholesky-QR2 and Rayleigh-Ritz
- * (Jacobi), all FP64; full Jacobi when n is small. */
+ * Block subspace iteration with Chebyshev filtering, Cholesky-QR2 and Rayleigh-Ritz, locking a
+ * Ritz pair once its residual |M u - lambda u| is at most 3e-13 lambda_1; when n is small all
+ * eigenpairs of M at once.  The small symmetric eigenproblems (the Rayleigh-Ritz matrix, or M)
+ * are solved by an FP32 Jacobi refined to FP64 accuracy (Ogita-Aishima iterative refinement),
+ * with an FP64 Jacobi as fallback; every other step is FP64.  ENOTCONV / EINTERNAL carry a
+ * detail string (tucker_last_error_detail). */
 int tucker_eig_topk(const double* d_M, int32_t n, int32_t J, const double* d_U0, double* d_U,
                     double* d_lambda, void* stream);
 
