@@ -337,6 +337,41 @@ def batched_leg(args):
           flush=True)
 
 
+def precision_leg(args):
+    """The precision form's workload: 2000^3 with 4e7 uniform nonzeros, core 100^3; HOOI and MP
+    for `--precision-passes` passes each, FP64 and mixed, on the same tensor (its orderings built
+    once, outside the timing).  Prints sweeps/s of both forms and the largest fit difference."""
+    import torch
+    from paper_0711_2023_gb300 import build, synth, tucker as tk
+    build.build()
+    dims, nnz, core = (2000, 2000, 2000), 40_000_000, (100, 100, 100)
+    X = synth.random_sparse_tensor(dims, nnz, synth.config_seed(3))
+    T = tk.tucker_tensor_create(torch.from_numpy(X.idx).cuda(), torch.from_numpy(X.val).cuda(),
+                                X.dims)
+    passes = args.precision_passes
+    # untimed warm-up: builds the orderings and the mixed form's FP32 copies, tunes the kernels
+    tk.tucker_hooi(T, core, tol=-np.inf, max_iter=1, precision="mixed")
+    tk.tucker_mp(T, core, tol=-np.inf, max_iter=1, precision="mixed")
+    res = {}
+    for prec in ("fp64", "mixed"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = tk.tucker_hooi(T, core, tol=-np.inf, max_iter=passes, precision=prec)
+        m = tk.tucker_mp(T, core, tol=-np.inf, max_iter=passes, precision=prec)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[prec] = {"sweeps_per_s": 2 * passes / dt, "seconds": dt,
+                     "fit_hooi": h["fit_history"], "fit_mp": m["fit_history"]}
+    dfit = max(abs(a - b) for k in ("fit_hooi", "fit_mp")
+               for a, b in zip(res["fp64"][k], res["mixed"][k]))
+    print(json.dumps({"leg": "precision", "workload": "2000^3, 4e7 uniform nonzeros, core 100^3, "
+                      f"HOOI + MP {passes} passes each", "fp64": res["fp64"],
+                      "mixed": res["mixed"],
+                      "speedup": res["mixed"]["sweeps_per_s"] / res["fp64"]["sweeps_per_s"],
+                      "max_abs_dfit": dfit, "unit": "sweeps/s",
+                      "note": "wall clock around the calls (they synchronise)"}), flush=True)
+
+
 def profile_leg(args):
     """One precision leg only (warm-up + timed steps), for profiler captures.  --profile-small
     uses a 500^3 tensor with 2.5e6 nonzeros and the same core (a few hundred MB on the device)."""
@@ -383,6 +418,9 @@ def main():
     ap.add_argument("--batched-leg", action="store_true",
                     help="time the batched workload (256 small tensors) instead")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--precision-leg", action="store_true",
+                    help="time HOOI and MP in FP64 and mixed on 2000^3 / 4e7 / core 100^3")
+    ap.add_argument("--precision-passes", type=int, default=2)
     args = ap.parse_args()
 
     world, rank, local = dist_setup(args.gpus)
@@ -394,6 +432,9 @@ def main():
         return
     if args.batched_leg:
         batched_leg(args)
+        return
+    if args.precision_leg:
+        precision_leg(args)
         return
 
     import torch
