@@ -76,24 +76,31 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        with open(self.path) as f:
+            return parse_clocks(f)
+
+
+def parse_clocks(lines):
+    """Summary of nvidia-smi samples (ClockSampler.QUERY, csv, no header, no units): median SM
+    clock under load, the maximum SM clock, and the throttle reasons seen active."""
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = float(parts[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 def dist_setup(n_gpus):
@@ -233,6 +240,20 @@ def roofline_of(prof, name, total_ms, bound, peak, unit, peak_source, per="flops
                              "capture x this launch's algorithmic bytes") if ratio else None,
             "algorithmic_bytes": d["bytes"] / d["launches"], "peak_source": peak_source,
             "share_of_step": d["ms"] / total_ms, "launches": d["launches"]}
+
+
+def ttmc_rates(pr, name, flop_peak, hbm_gbs):
+    """Algorithmic GB/s and TFLOP/s of one TTMc form from a profile, with their fractions."""
+    d = pr.get(name)
+    if not d or not d["ms"]:
+        return None
+    secs = d["ms"] * 1e-3
+    gbs, tfs = d["bytes"] / secs / 1e9, d["flops"] / secs / 1e12
+    return {"kernel": name, "launches": d["launches"], "ms_per_launch": d["ms"] / d["launches"],
+            "algorithmic_gbs": gbs, "frac_hbm": gbs / hbm_gbs if hbm_gbs else None,
+            "tflops": tfs, "frac_alu": tfs / flop_peak,
+            "note": "HOOI projection; at core 50 it does J_m J_o FMAs per fiber against 12 "
+                    "bytes of index data, so it is bound by arithmetic and row gathers, not HBM"}
 
 
 CPU_SAMPLE = "one HOOI pass (3 projections, Grams, eigensolves, core, fit) from the HO-SVD B, C"
@@ -498,17 +519,6 @@ def main():
     kp = kernels_only(prof)
     dom = max(kp, key=lambda k: kp[k]["ms"])
     roofline = roofline_of(prof, dom, prof_ms, "alu", FP64_PEAK_TFLOPS, "TFLOP/s", fp64_src)
-    def ttmc_rates(pr, name, flop_peak):
-        d = pr.get(name)
-        if not d or not d["ms"]:
-            return None
-        secs = d["ms"] * 1e-3
-        gbs, tfs = d["bytes"] / secs / 1e9, d["flops"] / secs / 1e12
-        return {"kernel": name, "launches": d["launches"], "ms_per_launch": d["ms"] / d["launches"],
-                "algorithmic_gbs": gbs, "frac_hbm": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs")
-                else None, "tflops": tfs, "frac_alu": tfs / flop_peak,
-                "note": "HOOI projection; at core 50 it does J_m J_o FMAs per fiber against 12 "
-                        "bytes of index data, so it is bound by arithmetic and row gathers, not HBM"}
     bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
     mx_gram = roofline_of(mx_prof, "gram_bf16x3", mx_prof_ms, "tensor", bf16, "TFLOP/s",
                           f"{peak_src} bf16 sustained (cuBLAS), algorithmic FP32-equivalent "
@@ -536,8 +546,9 @@ def main():
         "kernels": kern_table(prof, prof_ms),
         "profiled_step_ms": prof_ms,
         "eig_counters": prof["counters"],
-        "ttmc": {"fp64": ttmc_rates(prof, "ttmc_f64", FP64_PEAK_TFLOPS),
-                 "mixed": ttmc_rates(mx_prof, "ttmc_mixed", FP32_PEAK_TFLOPS)},
+        "ttmc": {"fp64": ttmc_rates(prof, "ttmc_f64", FP64_PEAK_TFLOPS, peaks.get("hbm_gbs")),
+                 "mixed": ttmc_rates(mx_prof, "ttmc_mixed", FP32_PEAK_TFLOPS,
+                                     peaks.get("hbm_gbs"))},
         "roofline": roofline,
         "mixed": {"value": mx_value, "unit": "sweeps/s", "ms_per_step": mx_ms / args.steps,
                   "speedup_vs_fp64": mx_value / value,
