@@ -7,10 +7,14 @@ is passes ("sweeps") per second: 31 per step (HO-SVD counts as one pass).
 
   value       device-resident: the COO tensor is in HBM before the timed region
   e2e         through the public C ABI with host buffers: pinned-host COO in, factors/core out
+  mixed       the same step in the mixed form (FP32 projections, tensor-core Gram), its speedup
+              and largest fit difference against the FP64 form
   roofline    dominant kernel, achieved = algorithmic FLOPs / its event-timed device time
   cpu_baseline  the FP64 oracle on this host's cores, on a bounded sample of the workload
 
 --impl reference times the oracle itself (CPU) on the same workload and metric.
+--batched-leg (256 small tensors), --precision-leg (2000^3, core 100^3, FP64 vs mixed) and
+--profile-leg fp64|mixed (one form only, for profiler captures) print their own lines.
 Multi-GPU (torchrun): each rank runs its own independent tensor (weak scaling, no collective).
 """
 from __future__ import annotations
