@@ -254,6 +254,13 @@ def hosvd(dims, idx, val, J):
     return _result(G, U, nX2, [fit_from_core(nX2, G)])
 
 
+def hooi_update(dims, idx, val, n, U, Jn):
+    """One factor update of Figure hooi3: the projection Y = X x_m U_m^T x_o U_o^T with the
+    newest other factors, and the J_n leading eigenvectors of Y_(n) Y_(n)^T.  Returns (U_n, Y)."""
+    Y = ttmc(dims, idx, val, n, U)
+    return leading_eigvecs(gram(unfold_dense(Y, n)), Jn)[0], Y
+
+
 def hooi(dims, idx, val, J, tol=1e-4, max_iter=50, init=None):
     """Figure hooi3 with the Delta_fit stop test.  B, C start from HO-SVD (or `init`); A is
     not initialised.  Each pass: U = [[X; I, B^T, C^T]] -> A; V = [[X; A^T, I, C^T]] -> B;
@@ -270,8 +277,7 @@ def hooi(dims, idx, val, J, tol=1e-4, max_iter=50, init=None):
     G = None
     for _ in range(max_iter):
         for n in MODES:
-            Y = ttmc(dims, idx, val, n, U)
-            U[n] = leading_eigvecs(gram(unfold_dense(Y, n)), J[n])[0]
+            U[n], Y = hooi_update(dims, idx, val, n, U, J[n])
         G = nmode_product_dense(Y, 2, U[2].T)             # W x_3 C^T = [[X; A^T, B^T, C^T]]
         f = fit_from_core(nX2, G)
         fits.append(f)
@@ -328,8 +334,24 @@ def mp_init_matrix(dims, idx, val, n):
     return M
 
 
-def mp(dims, idx, val, J, tol=1e-4, max_iter=50):
-    """Figure mp3 with the Delta_fit stop test.  Pseudo HO-SVD initialisation of B and C, then
+def mp_term(dims, idx, val, n, m, Um):
+    """One slice sum of Figure mp3 for output mode n: sum over the slices of X along the third
+    mode of X_s U_m U_m^T X_s^T, i.e. Gram((X x_m U_m^T)_(n))."""
+    return gram(unfold_dense(ttm(dims, idx, val, m, Um), n))
+
+
+def mp_update(dims, idx, val, n, U, Jn):
+    """One factor update of Figure mp3: the J_n leading eigenvectors of the sum, over the two
+    other modes m, of the slice sums Gram((X x_m U_m^T)_(n))."""
+    M = np.zeros((dims[n], dims[n]))
+    for m in other_modes(n):
+        M += mp_term(dims, idx, val, n, m, U[m])
+    return leading_eigvecs(M, Jn)[0]
+
+
+def mp(dims, idx, val, J, tol=1e-4, max_iter=50, init=None):
+    """Figure mp3 with the Delta_fit stop test.  Pseudo HO-SVD initialisation of B and C (or
+    `init`, as in hooi), then
     each pass
        M1 = Gram((X x_2 B^T)_(1)) + Gram((X x_3 C^T)_(1)) -> A
        M2 = Gram((X x_1 A^T)_(2)) + Gram((X x_3 C^T)_(2)) -> B
@@ -340,16 +362,15 @@ def mp(dims, idx, val, J, tol=1e-4, max_iter=50):
     idx, val, nX2 = _prep(dims, idx, val)
     U = [None, None, None]
     for n in (1, 2):
-        U[n] = leading_eigvecs(mp_init_matrix(dims, idx, val, n), J[n])[0]
+        if init is not None and init[n] is not None:
+            U[n] = np.asarray(init[n], dtype=np.float64)
+        else:
+            U[n] = leading_eigvecs(mp_init_matrix(dims, idx, val, n), J[n])[0]
     fits, old = [], 0.0
     G = None
     for _ in range(max_iter):
         for n in MODES:
-            M = np.zeros((dims[n], dims[n]))
-            for m in other_modes(n):
-                Y = ttm(dims, idx, val, m, U[m])
-                M += gram(unfold_dense(Y, n))
-            U[n] = leading_eigvecs(M, J[n])[0]
+            U[n] = mp_update(dims, idx, val, n, U, J[n])
         G = core(dims, idx, val, U)
         f = fit_from_core(nX2, G)
         fits.append(f)
@@ -364,3 +385,228 @@ def subspace_distance(U, V):
     U = np.asarray(U)
     V = np.asarray(V)
     return float(np.linalg.norm(U @ U.T - V @ V.T, 2))
+
+
+# ----------------------------------------------------------------------------------------------
+# Tensors of arbitrary order N (Figures HO-SVDn and hooin) and the fourth-order forms of Slice
+# Projection and Multislice Projection (Figures sp4 and mp4).  idx is N x nnz.  For N = 3 these
+# functions compute what the third-order ones above do.
+# ----------------------------------------------------------------------------------------------
+
+def canonical_coo_n(dims, idx, val):
+    """Sum duplicate coordinates of an order-N COO tensor; returns (idx, val) sorted
+    lexicographically by (i_1, ..., i_N), duplicates added in their original COO order."""
+    idx = np.asarray(idx, dtype=np.int64)
+    val = np.asarray(val, dtype=np.float64)
+    order = np.lexsort(tuple(idx[a] for a in reversed(range(idx.shape[0]))))
+    idx, val = idx[:, order], val[order]
+    if idx.shape[1] == 0:
+        return idx, val
+    new = np.ones(idx.shape[1], dtype=bool)
+    new[1:] = np.any(idx[:, 1:] != idx[:, :-1], axis=0)
+    starts = np.flatnonzero(new)
+    sums = np.zeros(starts.shape[0])
+    np.add.at(sums, np.cumsum(new) - 1, val)
+    return idx[:, starts], sums
+
+
+def to_dense_n(dims, idx, val):
+    X = np.zeros(dims)
+    np.add.at(X, tuple(np.asarray(i) for i in idx), val)
+    return X
+
+
+def _rest(N, n):
+    return tuple(a for a in range(N) if a != n)
+
+
+def unfolding_gram_n(dims, idx, val, n):
+    """X_(n) X_(n)^T of an order-N sparse tensor (Figure HO-SVDn)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    rest = _rest(len(dims), n)
+    cols = np.zeros(idx.shape[1], dtype=np.int64)
+    for a in rest:
+        cols = cols * dims[a] + idx[a]
+    ncol = int(np.prod([dims[a] for a in rest]))
+    Xn = sps.csr_matrix((np.asarray(val, dtype=np.float64), (idx[n], cols)),
+                        shape=(dims[n], ncol))
+    return np.asarray((Xn @ Xn.T).todense())
+
+
+def ttm_n(dims, idx, val, m, U):
+    """Y = X x_m U^T for an order-N sparse X (eq. 1): a dense N-way array with mode m of size
+    J_m.  (Figures sp4 and mp4: the slice sums over the other modes equal Gram(Y_(n)).)"""
+    U = np.asarray(U, dtype=np.float64)
+    idx = np.asarray(idx, dtype=np.int64)
+    N = len(dims)
+    rest = _rest(N, m)
+    rows = np.zeros(idx.shape[1], dtype=np.int64)
+    for a in rest:
+        rows = rows * dims[a] + idx[a]
+    nrow = int(np.prod([dims[a] for a in rest]))
+    Xm = sps.csr_matrix((np.asarray(val, dtype=np.float64), (rows, idx[m])), shape=(nrow, dims[m]))
+    Z = np.asarray(Xm @ U)                                   # (prod rest) x J_m
+    Z = Z.reshape([dims[a] for a in rest] + [U.shape[1]])
+    return np.moveaxis(Z, N - 1, m)
+
+
+def ttmc_n(dims, idx, val, n, U):
+    """Z = [[X; U_1^T, ..., I_n, ..., U_N^T]] (Figure hooin): every mode but n projected onto
+    its factor.  One sparse product on the last projected mode, dense products for the rest."""
+    N = len(dims)
+    rest = _rest(N, n)
+    T = ttm_n(dims, idx, val, rest[-1], U[rest[-1]])
+    for a in rest[:-1]:
+        T = nmode_product_dense(T, a, np.asarray(U[a]).T)
+    return T
+
+
+def core_n(dims, idx, val, U):
+    """G = [[X; U_1^T, ..., U_N^T]] for an order-N tensor."""
+    T = ttmc_n(dims, idx, val, 0, U)
+    return nmode_product_dense(T, 0, np.asarray(U[0]).T)
+
+
+def fit_explicit_n(dims, idx, val, G, U):
+    """fit = 1 - |X - [[G; U_1, ..., U_N]]|_F / |X|_F, reconstructed densely (small only)."""
+    X = to_dense_n(dims, idx, val)
+    Xh = np.asarray(G)
+    for a in range(len(dims)):
+        Xh = nmode_product_dense(Xh, a, U[a])
+    return 1.0 - np.linalg.norm((X - Xh).ravel()) / np.linalg.norm(X.ravel())
+
+
+def _prep_n(dims, idx, val, J):
+    N = len(dims)
+    for a in range(N):
+        if not (1 <= J[a] <= dims[a]):
+            raise ValueError("core size out of range")
+    idx, val = canonical_coo_n(dims, idx, val)
+    nX2 = norm2(val)
+    if nX2 == 0.0:
+        raise ValueError("empty tensor: |X| = 0 makes the fit undefined")
+    return idx, val, nX2
+
+
+def hosvd_n(dims, idx, val, J):
+    """Figure HO-SVDn: A^(n) <- J_n leading eigenvectors of X_(n) X_(n)^T for every n, then the
+    core."""
+    idx, val, nX2 = _prep_n(dims, idx, val, J)
+    U = [leading_eigvecs(unfolding_gram_n(dims, idx, val, n), J[n])[0] for n in range(len(dims))]
+    G = core_n(dims, idx, val, U)
+    return _result(G, U, nX2, [fit_from_core(nX2, G)])
+
+
+def hooi_n(dims, idx, val, J, tol=1e-4, max_iter=50, init=None):
+    """Figure hooin with the Delta_fit stop test: A^(2..N) from HO-SVD (or `init`), then per pass
+    for n = 1..N: Z = [[X; A^(1)T, ..., I_n, ..., A^(N)T]] with the newest factors and
+    A^(n) <- J_n leading eigenvectors of Z_(n) Z_(n)^T; then G and the fit."""
+    idx, val, nX2 = _prep_n(dims, idx, val, J)
+    N = len(dims)
+    U = [None] * N
+    for n in range(1, N):
+        if init is not None and init[n] is not None:
+            U[n] = np.asarray(init[n], dtype=np.float64)
+        else:
+            U[n] = leading_eigvecs(unfolding_gram_n(dims, idx, val, n), J[n])[0]
+    fits, old, G = [], 0.0, None
+    for _ in range(max_iter):
+        for n in range(N):
+            Z = ttmc_n(dims, idx, val, n, U)
+            U[n] = leading_eigvecs(gram(unfold_dense(Z, n)), J[n])[0]
+        G = nmode_product_dense(Z, N - 1, U[N - 1].T)   # the last Z projected on the last mode
+        f = fit_from_core(nX2, G)
+        fits.append(f)
+        if f - old < tol:
+            break
+        old = f
+    return _result(G, U, nX2, fits)
+
+
+# Figure sp4: A from the slices on modes 2, 3 projected with D (M14), B from those on 3, 4 with
+# A (M21), C from those on 1, 4 with B (M32), D from those on 1, 2 with C (M43): 0-based pairs
+# (updated mode, projecting mode).
+SP4_PAIRS = ((0, 3), (1, 0), (2, 1), (3, 2))
+
+
+def sp4(dims, idx, val, J, D_raw, tol=1e-4, max_iter=50):
+    """Figure sp4 with the Delta_G stop test.  D starts as the random matrix with normalised
+    columns; each pass M_nm = sum over the slices of X_s U_m U_m^T X_s^T = Gram((X x_m U_m^T)_(n))
+    for the pairs of SP4_PAIRS in order, U_n <- J_n leading eigenvectors of M_nm; then G."""
+    if len(dims) != 4:
+        raise ValueError("sp4 takes a fourth-order tensor")
+    idx, val, nX2 = _prep_n(dims, idx, val, J)
+    U = [None, None, None, sp_initial_C(D_raw)]
+    fits, gnorms, G = [], [], None
+    for t in range(max_iter):
+        for n, m in SP4_PAIRS:
+            Y = ttm_n(dims, idx, val, m, U[m])
+            U[n] = leading_eigvecs(gram(unfold_dense(Y, n)), J[n])[0]
+        G = core_n(dims, idx, val, U)
+        gn = float(np.linalg.norm(G.ravel()))
+        fits.append(fit_from_core(nX2, G))
+        gnorms.append(gn)
+        if t >= 1 and (1.0 - gnorms[-2] / gn) < tol:
+            break
+    return _result(G, U, nX2, fits, dict(gnorm_history=gnorms))
+
+
+def mp4_init_matrix(dims, idx, val, n):
+    """Pseudo HO-SVD matrix of Figure mp4, as written: for mode n, the sum over the three ways of
+    choosing a second free mode r of the slice Gram sums sum_s X_s X_s^T, the slices X_s being
+    the I_n x I_r matrices obtained by fixing the two remaining modes."""
+    idx = np.asarray(idx, dtype=np.int64)
+    val = np.asarray(val, dtype=np.float64)
+    N = len(dims)
+    M = np.zeros((dims[n], dims[n]))
+    for r in _rest(N, n):
+        fixed = [a for a in range(N) if a not in (n, r)]
+        key = idx[fixed[0]] * dims[fixed[1]] + idx[fixed[1]]
+        order = np.argsort(key, kind="stable")
+        bounds = np.searchsorted(key[order], np.arange(dims[fixed[0]] * dims[fixed[1]] + 1))
+        for t in range(dims[fixed[0]] * dims[fixed[1]]):
+            sel = order[bounds[t]:bounds[t + 1]]
+            if sel.size == 0:
+                continue
+            Xt = sps.csr_matrix((val[sel], (idx[n][sel], idx[r][sel])), shape=(dims[n], dims[r]))
+            M += np.asarray((Xt @ Xt.T).todense())
+    return M
+
+
+def mp4_matrix(dims, idx, val, n, U):
+    """The matrix M_n of a pass of Figure mp4: the sum, over the three other modes m, of the
+    slice sums sum_s X_s U_m U_m^T X_s^T = Gram((X x_m U_m^T)_(n))."""
+    M = np.zeros((dims[n], dims[n]))
+    for m in _rest(len(dims), n):
+        M += gram(unfold_dense(ttm_n(dims, idx, val, m, U[m]), n))
+    return M
+
+
+def mp4_update(dims, idx, val, n, U, Jn):
+    """One factor update of Figure mp4: the J_n leading eigenvectors of mp4_matrix."""
+    return leading_eigvecs(mp4_matrix(dims, idx, val, n, U), Jn)[0]
+
+
+def mp4(dims, idx, val, J, tol=1e-4, max_iter=50, init=None):
+    """Figure mp4 with the Delta_fit stop test: B, C, D from the pseudo HO-SVD matrices (or
+    `init`), then per pass A, B, C, D by mp4_update with the newest factors; then G, fit."""
+    if len(dims) != 4:
+        raise ValueError("mp4 takes a fourth-order tensor")
+    idx, val, nX2 = _prep_n(dims, idx, val, J)
+    U = [None] * 4
+    for n in (1, 2, 3):
+        if init is not None and init[n] is not None:
+            U[n] = np.asarray(init[n], dtype=np.float64)
+        else:
+            U[n] = leading_eigvecs(mp4_init_matrix(dims, idx, val, n), J[n])[0]
+    fits, old, G = [], 0.0, None
+    for _ in range(max_iter):
+        for n in range(4):
+            U[n] = mp4_update(dims, idx, val, n, U, J[n])
+        G = core_n(dims, idx, val, U)
+        f = fit_from_core(nX2, G)
+        fits.append(f)
+        if f - old < tol:
+            break
+        old = f
+    return _result(G, U, nX2, fits)

@@ -182,3 +182,69 @@ def planted_tensor(dims, core, support, seed: int):
     idx = np.stack([ii.ravel(), jj.ravel(), kk.ravel()])[:, order].astype(np.int32)
     val = sub.ravel()[order].astype(np.float64)
     return CooTensor(tuple(dims), idx, val), G, factors
+
+
+def random_sparse_tensor_n(dims, nnz: int, seed: int) -> CooTensor:
+    """Order-N form of random_sparse_tensor (same scheme: the first `nnz` distinct linear
+    indices floor(u * prod(dims) / 2**64) in stream order, values U[0,1) from a second stream;
+    for N = 3 the result equals random_sparse_tensor's).  idx is int32 [N, nnz]."""
+    dims = tuple(int(d) for d in dims)
+    N = int(np.prod(dims))
+    if nnz > N:
+        raise ValueError("nnz exceeds the number of cells")
+    s_coord = splitmix64_scalar(seed ^ 0x636F6F7264)
+    s_val = splitmix64_scalar(seed ^ 0x76616C)
+    chosen = np.empty(0, dtype=np.int64)
+    drawn = 0
+    while chosen.shape[0] < nnz:
+        need = nnz - chosen.shape[0]
+        batch = max(1024, int(need * (1.0 + 2.0 * nnz / N)) + 64)
+        lin = _mulhi(splitmix64(s_coord, batch, offset=drawn), N).astype(np.int64)
+        drawn += batch
+        allc = np.concatenate([chosen, lin])
+        _, first = np.unique(allc, return_index=True)
+        first.sort()
+        chosen = allc[first][:nnz]
+    idx = np.empty((len(dims), nnz), dtype=np.int64)
+    rem = chosen
+    for a in reversed(range(len(dims))):
+        idx[a] = rem % dims[a]
+        rem = rem // dims[a]
+    val = uniform01(splitmix64(s_val, nnz))
+    return CooTensor(dims, idx.astype(np.int32), val)
+
+
+def planted_tensor_n(dims, core, support, seed: int):
+    """Order-N form of planted_tensor: X = G x1 U1 x2 U2 ... with random G and orthonormal
+    factors whose rows vanish outside random support sets.  Returns (CooTensor, G, factors)."""
+    rng_u = uniform01(splitmix64(seed, 1 << 21))
+    pos = [0]
+
+    def take(n):
+        a = rng_u[pos[0]:pos[0] + n]
+        pos[0] += n
+        return a
+
+    def gauss(shape):
+        n = int(np.prod(shape))
+        u1, u2 = take(n), take(n)
+        return (np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)).reshape(shape)
+
+    N = len(dims)
+    factors, supports = [], []
+    for a in range(N):
+        sup = np.sort(np.argsort(take(dims[a]), kind="stable")[:support[a]])
+        Q, _ = np.linalg.qr(gauss((support[a], core[a])))
+        U = np.zeros((dims[a], core[a]))
+        U[sup] = Q
+        factors.append(U)
+        supports.append(sup)
+    G = gauss(tuple(core))
+    sub = G
+    for a in range(N):   # sub = G x_a U_a[support], mode by mode
+        sub = np.moveaxis(np.tensordot(factors[a][supports[a]], sub, axes=(1, a)), 0, a)
+    grids = np.meshgrid(*supports, indexing="ij")
+    order = np.argsort(take(sub.size), kind="stable")
+    idx = np.stack([g.ravel() for g in grids])[:, order].astype(np.int32)
+    val = sub.ravel()[order].astype(np.float64)
+    return CooTensor(tuple(dims), idx, val), G, factors
