@@ -62,7 +62,8 @@ typedef struct {
   double tol;            /* stop threshold of the Delta_fit / Delta_G test; -INFINITY = never */
   int32_t max_iter;      /* passes of the main loop (>= 1; ignored by HO-SVD) */
   const double* init[3]; /* optional starting factors, I_n x J_n (NULL = the method's own).
-                            HOOI: init[1], init[2] replace the HO-SVD start of B and C.
+                            HOOI, MP: init[1], init[2] replace the start of B and C
+                                  (HOOI's HO-SVD start, MP's pseudo HO-SVD start).
                             SP:   init[2] is the REQUIRED raw random I3 x J3 matrix of
                                   Figure sp3; the library normalises its columns. */
   int32_t init_where;    /* tucker_mem of init[] */
@@ -115,6 +116,62 @@ int tucker_hooi_batched(int32_t count, const tucker_tensor* Xs, const int32_t* J
 int tucker_mp_batched(int32_t count, const tucker_tensor* Xs, const int32_t* J,
                       const tucker_opts* opts, tucker_result* out);
 
+/* ---- fourth-order tensors -------------------------------------------------------------------
+ * HO-SVD and HOOI for N = 4 (Figures HO-SVDn and hooin), Slice Projection and Multislice
+ * Projection for fourth-order tensors (Figures sp4 and mp4), in the FP64 form (precision must be
+ * TUCKER_FP64, else EINVAL).  Conventions as above with four modes: factor n is I_n x J_n
+ * row-major, the core g[((p J2 + q) J3 + r) J4 + s].  Stop tests as for third order (HOOI, MP:
+ * signed Delta_fit with fit_0 = 0; SP: Delta_G from the second pass).  SP's init[3] is the
+ * REQUIRED raw random I4 x J4 matrix of Figure sp4 (columns normalised by the library); for
+ * HOOI and MP, init[1..3] may replace the start of B, C, D (HO-SVD's; MP's pseudo HO-SVD matrices
+ * equal 3 X_(n) X_(n)^T and have the same leading eigenvectors).  Limits: every I_a I_b < 2^31
+ * (two modes are merged into one index internally), I1 I2 I3 I4 < 2^62. */
+typedef struct {
+  int64_t dims[4];
+  int64_t nnz;
+  const int32_t* idx[4];
+  const double* val;
+  int32_t where;
+} tucker4_coo;
+
+typedef struct {
+  int32_t precision;
+  double tol;
+  int32_t max_iter;
+  const double* init[4];
+  int32_t init_where;
+  void* stream;
+  uint32_t flags;
+} tucker4_opts;
+
+typedef struct {
+  double* G;             /* J1*J2*J3*J4 */
+  double* U[4];          /* I_n * J_n */
+  double* fit_history;   /* optional, max_iter entries */
+  int32_t where;
+  double fit;
+  int32_t iters;
+  int32_t rank_deficient;
+} tucker4_result;
+
+typedef struct tucker4_tensor_s* tucker4_tensor;
+
+/* Copies X to the device, checks every index (EINVAL), sums duplicates, computes |X|_F^2. */
+int tucker4_tensor_create(const tucker4_coo* X, void* stream, tucker4_tensor* out);
+int tucker4_tensor_destroy(tucker4_tensor X);
+int tucker4_tensor_info(tucker4_tensor X, int64_t* nnz, double* norm2);
+int tucker4_hosvd(tucker4_tensor X, const int32_t J[4], const tucker4_opts* opts,
+                  tucker4_result* out);
+int tucker4_hooi(tucker4_tensor X, const int32_t J[4], const tucker4_opts* opts,
+                 tucker4_result* out);
+int tucker4_sp(tucker4_tensor X, const int32_t J[4], const tucker4_opts* opts, tucker4_result* out);
+int tucker4_mp(tucker4_tensor X, const int32_t J[4], const tucker4_opts* opts, tucker4_result* out);
+/* HOOI's projection of Figure hooin for N = 4: Z = [[X; U_1^T, ..., I_n, ..., U_4^T]] written as
+ * Z_(n), I_n x (J_a J_b J_c) row-major with column (p J_b + q) J_c + r for the other modes
+ * a < b < c.  d_U[n] is not read (may be NULL).  Device pointers; synchronous on stream. */
+int tucker4_ttmc(tucker4_tensor X, int32_t n, const double* const d_U[4], const int32_t J[4],
+                 double* d_Y, void* stream);
+
 const char* tucker_strerror(int status);
 /* Text of the last CUDA failure seen by the calling thread (empty if none). */
 const char* tucker_last_error_detail(void);
@@ -146,9 +203,24 @@ int tucker_slice_proj(tucker_tensor X, int32_t n, int32_t m, const double* d_Um,
                       double* d_Y, void* stream);
 
 /* Gram M = Y1 Y1^T (+ Y2 Y2^T when d_Y2 != NULL): Y1 is rows x K1, Y2 rows x K2, row-major;
- * M is rows x rows (both triangles written). */
+ * M is rows x rows (both triangles written).  Computed on the BF16 tensor cores to FP64
+ * accuracy: every row is scaled by a power of two and cut into seven 7-bit integer slices
+ * (error-free splitting, Ozaki et al. 2012); the 28 slice products that reach 2^-49 of the
+ * leading term are summed exactly (integer-valued FP32 chunks, 64-bit integer totals), so the
+ * error is a few units of 2^-49 |y_i| |y_j| per entry and the result does not depend on how K
+ * is split.  d_Y1 may be NULL when K1 = 0 (M = 0).  ETIMEOUT if a bounded wait inside the
+ * kernel gave up. */
 int tucker_gram(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2, int32_t rows,
                 double* d_M, void* stream);
+
+/* C = A B (A: m x K, ld lda; B: K x n, ld ldb; C: m x n, ld ldc; row-major, device), computed
+ * on the BF16 tensor cores with the error-free slicing of tucker_gram: every row of A and every
+ * column of B is scaled by a power of two and cut into seven 7-bit slices, so the error of
+ * C[i][j] is a few units of 2^-49 max_k |A[i][k]| max_k |B[k][j]| (times sqrt(K) at most for
+ * uncorrelated errors).  The eigensolver's products with M (M V) use it.  d_A, d_B may be NULL
+ * when K = 0 (C = 0). */
+int tucker_gemm(const double* d_A, int64_t lda, const double* d_B, int64_t ldb, int32_t m,
+                int32_t n, int64_t K, double* d_C, int64_t ldc, void* stream);
 
 /* Allocation-free tucker_gram (the paper has no counterpart: this serves callers that cannot
  * let a library allocate device memory while they run, such as serving processes that reserve
@@ -157,8 +229,10 @@ int tucker_gram(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2, 
  * workspace is one fixed array of 2^21 doubles (16 MiB) that every GPU loading the library
  * holds until exit, so rows * rows must be <= 2^21 (rows <= 1448), else TUCKER_EINVAL.  The
  * first call on a device looks up the array's address (cudaGetSymbolAddress): make it before
- * any stream capture.  Calls share the array: calls that overlap on the GPU race; order them
- * on one stream. */
+ * any stream capture.  The address is kept for the life of the process, so the library does
+ * not support a cudaDeviceReset between calls.  Like every entry point, the call is
+ * synchronous: it returns once M is written.  Calls share the array: calls that overlap on the
+ * GPU race; order them on one stream. */
 int tucker_gram_noalloc(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2,
                         int32_t rows, double* d_M, void* stream);
 
@@ -190,7 +264,8 @@ int tucker_gram_bf16x3(const uint16_t* d_Y1hi, const uint16_t* d_Y1lo, int64_t K
  * (n x J, may be NULL) is a starting guess.  Outputs d_U (n x J) and d_lambda (J).
  * Block subspace iteration with Chebyshev filtering, Cholesky-QR2 and Rayleigh-Ritz, locking a
  * Ritz pair once its residual |M u - lambda u| is at most 3e-13 lambda_1; when n is small all
- * eigenpairs of M at once.  The small symmetric eigenproblems (the Rayleigh-Ritz matrix, or M)
+ * eigenpairs of M at once.  Its larger products (M V, V^T W, ...) run FP64-accurate on the
+ * tensor cores, like tucker_gram.  The small symmetric eigenproblems (the Rayleigh-Ritz matrix, or M)
  * are solved by an FP32 Jacobi refined to FP64 accuracy (Ogita-Aishima iterative refinement),
  * with an FP64 Jacobi as fallback; every other step is FP64.  ENOTCONV / EINTERNAL carry a
  * detail string (tucker_last_error_detail). */
@@ -206,7 +281,10 @@ int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const dou
  * launching stream around the hot-path kernels; 0 stops.  tucker_profile_query sums, for the
  * record `name`, the launches recorded, their device time in milliseconds and their
  * algorithmic FLOPs and bytes (what the method must compute and move, not what the kernel
- * happens to do).  Timed records: the kernels "syrk_f64", "gram_bf16x3", "ttmc_f64",
+ * happens to do).  Timed records: "gram_f64_tc" (the whole FP64 Gram: splitting, tensor-core
+ * products, reduction) with its kernels "ozaki_split" and "gram_ozaki" (flops: the BF16 FLOPs
+ * its tensor cores issue), "gemm_ozaki" (the eigensolver's FP64 products on the tensor cores,
+ * flops likewise), the kernels "syrk_f64", "gram_bf16x3", "ttmc_f64",
  * "ttmc_mixed", "slice_proj_f64", "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64",
  * "gemm_nn_f32", "gemm_tn_f64", "chol_f64", "jacobi_f64", "csf_build", and the stages
  * "eig_topk" (one leading-eigenvector solve) and "syev_refined" (one small eigenproblem) with

@@ -137,6 +137,18 @@ void other_modes(int n, int* m, int* o) {
 
 }  // namespace
 
+int fit_on_device(double nX2, const double* g2_dev, double* fit_dev, cudaStream_t s) {
+  fit_kernel<<<1, 32, 0, s>>>(nX2, g2_dev, fit_dev);
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+int normalize_columns(const double* src, int rows, int cols, double* dst, cudaStream_t s) {
+  normalize_cols<<<cols, 256, 0, s>>>(src, rows, cols, dst);
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
 int core_from_ttmc3(const double* Y3, int I3, int J1, int J2, const double* C, int J3, double* G,
                     double* g2_dev, cudaStream_t s) {
   // G[(p J2 + q) J3 + r] = sum_k Y3[k, p J2 + q] C[k, r]  (G = W x_3 C^T, Figure hooi3).
@@ -269,7 +281,7 @@ int hooi_matrix(Run& r, int n) {
   if (!r.mixed) {
     TK_TRY(ttmc_f64(r.X, ord, r.U[m].as<double>(), r.J[m], r.U[o].as<double>(), r.J[o],
                     r.Y.as<double>(), r.s));
-    return syrk_f64((int)r.dim(n), r.Y.as<double>(), K, nullptr, 0, r.M.as<double>(), r.s);
+    return gram_f64_tc((int)r.dim(n), r.Y.as<double>(), K, nullptr, 0, r.M.as<double>(), r.s);
   }
   const int64_t ld = gram_ld(K);
   __nv_bfloat16 *yh = r.Yh.as<__nv_bfloat16>(), *yl = r.Yl.as<__nv_bfloat16>();
@@ -308,8 +320,9 @@ int slice_matrix(Run& r, int n, int m1, int m2) {
   const int nt = m2 >= 0 ? 2 : 1;
   if (nt == 2) TK_TRY(slice_term(r, n, m2, 1, &t[1]));
   if (!r.mixed)
-    return syrk_f64((int)r.dim(n), r.Y.as<double>(), t[0].K, nt == 2 ? r.Y2.as<double>() : nullptr,
-                    nt == 2 ? t[1].K : 0, r.M.as<double>(), r.s);
+    return gram_f64_tc((int)r.dim(n), r.Y.as<double>(), t[0].K,
+                       nt == 2 ? r.Y2.as<double>() : nullptr, nt == 2 ? t[1].K : 0,
+                       r.M.as<double>(), r.s);
   return gram_bf16x3((int)r.dim(n), nt, t, r.M.as<double>(), r.s);
 }
 
@@ -438,16 +451,15 @@ int run_method(Method method, tucker_tensor_s* X, const int32_t J[3], const tuck
     TK_TRY(raw.alloc(sizeof(double) * r.dim(2) * J[2], r.s));
     TK_CUDA(cudaMemcpyAsync(raw.p, r.o.init[2], sizeof(double) * r.dim(2) * J[2],
                             kind_to_device(r.o.init_where), r.s));
-    normalize_cols<<<J[2], 256, 0, r.s>>>(raw.as<double>(), (int)r.dim(2), J[2],
-                                          r.U[2].as<double>());
-    TK_LAUNCH();
+    TK_TRY(normalize_columns(raw.as<double>(), (int)r.dim(2), J[2], r.U[2].as<double>(), r.s));
     TK_TRY(refresh32(r, 2));
     TK_CUDA(cudaStreamSynchronize(r.s));
   } else {
-    // HOOI: B, C from HO-SVD (or given).  MP: pseudo HO-SVD; each of its two slice sums equals
-    // X_(n) X_(n)^T (Figure mp3), so the matrix is 2 X_(n) X_(n)^T.
+    // HOOI: B, C from HO-SVD.  MP: pseudo HO-SVD; each of its two slice sums equals
+    // X_(n) X_(n)^T (Figure mp3), so the matrix is 2 X_(n) X_(n)^T.  Either start is replaced by
+    // the caller's B, C when given.
     for (int n = 1; n < 3; ++n) {
-      if (method == Method::HOOI) {
+      {
         const int li = load_init(r, n);
         if (li < 0) return TUCKER_ECUDA;
         if (li > 0) {
@@ -538,6 +550,9 @@ int run_batched(Method method, int32_t count, const tucker_tensor* Xs, const int
   for (int i = 0; i < nthreads; ++i)
     TK_CUDA(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking));
   std::vector<int> status(count, TUCKER_OK);
+  // The error detail is per thread: a worker keeps the text of each failing tensor so that the
+  // caller's thread can report the one whose status it returns.
+  std::vector<std::string> detail(count);
   std::vector<std::thread> pool;
   for (int i = 0; i < nthreads; ++i)
     pool.emplace_back([&, i]() {
@@ -547,13 +562,19 @@ int run_batched(Method method, int32_t count, const tucker_tensor* Xs, const int
       }
       tucker_opts o = base;
       o.stream = streams[i];
-      for (int t = i; t < count; t += nthreads)
+      for (int t = i; t < count; t += nthreads) {
+        g_last_error.clear();
         status[t] = run_method(method, Xs[t], J + 3 * (int64_t)t, &o, &out[t]);
+        if (status[t] != TUCKER_OK) detail[t] = g_last_error;
+      }
     });
   for (auto& th : pool) th.join();
   for (auto st : streams) cudaStreamDestroy(st);
   for (int t = 0; t < count; ++t)
-    if (status[t] != TUCKER_OK) return status[t];
+    if (status[t] != TUCKER_OK) {
+      g_last_error = detail[t];
+      return status[t];
+    }
   return TUCKER_OK;
 }
 
@@ -734,10 +755,34 @@ int tucker_slice_proj(tucker_tensor X, int32_t n, int32_t m, const double* d_Um,
 
 int tucker_gram(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2, int32_t rows,
                 double* d_M, void* stream) {
-  if (!d_Y1 || !d_M || rows < 1 || K1 < 0 || (d_Y2 && K2 < 0)) return TUCKER_EINVAL;
+  if ((!d_Y1 && K1 != 0) || !d_M || rows < 1 || K1 < 0 || (d_Y2 && K2 < 0)) return TUCKER_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  TK_TRY(syrk_f64(rows, d_Y1, K1, d_Y2, d_Y2 ? K2 : 0, d_M, s));
+  TK_TRY(gram_f64_tc(rows, d_Y1, K1, d_Y2, d_Y2 ? K2 : 0, d_M, s));
   TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+int tucker_gemm(const double* d_A, int64_t lda, const double* d_B, int64_t ldb, int32_t m,
+                int32_t n, int64_t K, double* d_C, int64_t ldc, void* stream) {
+  if (!d_C || m < 1 || n < 1 || K < 0 || (K > 0 && (!d_A || !d_B)) || lda < K || ldb < n ||
+      ldc < n)
+    return TUCKER_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  OzSlices a, b;
+  TK_TRY(oz_split_rows(d_A, lda, m, K, nullptr, 0, 0, OZ_GEMM_SLICES, &a, s));
+  TK_TRY(oz_split_cols(d_B, ldb, K, n, OZ_GEMM_SLICES, &b, s));
+  Buf st;
+  TK_TRY(st.alloc(sizeof(int), s));
+  TK_CUDA(cudaMemsetAsync(st.p, 0, sizeof(int), s));
+  TK_TRY(oz_gemm_nt(a, b, false, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, d_C, ldc, st.as<int>(), s,
+                    "gemm_ozaki"));
+  int h = 0;
+  TK_CUDA(cudaMemcpyAsync(&h, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  if (h & DEV_TIMEOUT) {
+    set_error_detail("tensor-core product: a bounded wait on an mbarrier gave up");
+    return TUCKER_ETIMEOUT;
+  }
   return TUCKER_OK;
 }
 

@@ -333,6 +333,11 @@ __global__ void sum_partials(const double* __restrict__ part, int n, double* __r
 
 }  // namespace
 
+int exclusive_scan_u32(const unsigned* in, unsigned* out, int64_t n, unsigned* d_total,
+                       cudaStream_t s) {
+  return exclusive_scan<unsigned>(in, out, n, d_total, s);
+}
+
 int sum_squares(const double* d_v, int64_t n, double* d_out, cudaStream_t s) {
   const int nb = 1024;
   Buf part;

@@ -715,6 +715,77 @@ int sort_eig_desc(const double* Q, int64_t ldq, int m, const double* ev, double*
 
 namespace {
 
+// The eigensolver's dense products.  Those of at least OZ_MIN_FLOPS run FP64-accurate on the
+// tensor cores (gram_ozaki.cu: error-free slices, exact integer sums), with the slices of the
+// filter operator cut once per operator; smaller ones run on the CUDA cores (FP32 in the mixed
+// form's filter, FP64 otherwise).
+constexpr double OZ_MIN_FLOPS = 2e7;
+
+struct EigOps {
+  cudaStream_t s = 0;
+  int n = 0;
+  const double* mop = nullptr;   // operator whose row slices are in msl (nullptr: none)
+  OzSlices msl, a, b;
+  int* status = nullptr;         // device word: DEV_TIMEOUT from the tensor-core kernels
+  void invalidate() { mop = nullptr; }
+};
+
+// C (n x cols) = alpha Mop V + beta X + gamma Z, V n x cols (ld ldv).  With Mop32 (the mixed
+// form's filter, which needs only FP32 accuracy) the product runs in FP32 on the CUDA cores.
+int op_mv(EigOps& e, const double* Mop, const float* Mop32, const double* V, int64_t ldv,
+          int cols, double alpha, double beta, const double* X, int64_t ldx, double gamma,
+          const double* Z, int64_t ldz, double* C, int64_t ldc) {
+  const int n = e.n;
+  if (Mop32)
+    return gemm_nn_f32a(n, cols, n, alpha, Mop32, n, V, ldv, beta, X, ldx, gamma, Z, ldz, C, ldc,
+                        e.s);
+  if (2.0 * n * (double)n * cols >= OZ_MIN_FLOPS) {
+    if (e.mop != Mop) {
+      TK_TRY(oz_split_rows(Mop, n, n, n, nullptr, 0, 0, OZ_GEMM_SLICES, &e.msl, e.s));
+      e.mop = Mop;
+    }
+    TK_TRY(oz_split_cols(V, ldv, n, cols, OZ_GEMM_SLICES, &e.b, e.s));
+    return oz_gemm_nt(e.msl, e.b, false, alpha, beta, X, ldx, gamma, Z, ldz, C, ldc, e.status,
+                      e.s, "gemm_ozaki");
+  }
+  return gemm_nn_f64(n, cols, n, alpha, Mop, n, V, ldv, beta, X, ldx, gamma, Z, ldz, C, ldc, e.s);
+}
+
+// C (ka x kb, ld ldc) = A^T B with A: K x ka (ld lda), B: K x kb (ld ldb).
+int op_tn(EigOps& e, int ka, int kb, int64_t K, const double* A, int64_t lda, const double* B,
+          int64_t ldb, double* C, int64_t ldc) {
+  if (2.0 * ka * (double)kb * K >= OZ_MIN_FLOPS) {
+    TK_TRY(oz_split_cols(A, lda, K, ka, OZ_GEMM_SLICES, &e.a, e.s));
+    if (A == B && lda == ldb && ka == kb)
+      return oz_gemm_nt(e.a, e.a, true, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, C, ldc, e.status,
+                        e.s, "gemm_ozaki");
+    TK_TRY(oz_split_cols(B, ldb, K, kb, OZ_GEMM_SLICES, &e.b, e.s));
+    return oz_gemm_nt(e.a, e.b, false, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, C, ldc, e.status,
+                      e.s, "gemm_ozaki");
+  }
+  return gemm_tn_f64(ka, kb, K, A, lda, B, ldb, C, ldc, e.s);
+}
+
+// C (m x cols) = alpha A B + beta X + gamma Z with A: m x K (ld lda), B: K x cols (ld ldb).
+// The tensor-core products scale every row of A by its largest entry, so their error in C[i][j]
+// is relative to max_k |A[i][k]| max_k |B[k][j]|.  In the solver's N-N products (V Q, W Q, the
+// deflation) the rows of A mix columns of very different size (W = M V: row i is dominated by
+// the theta_1 column), and the Ritz residuals of the small-theta columns need accuracy relative
+// to their own size; those products have K <= k (small), so they run on the CUDA cores in FP64.
+// Only long-K N-N products (not used by the solver today) go to the tensor cores.
+constexpr int OZ_NN_MIN_K = 1024;
+int op_nn(EigOps& e, int m, int cols, int K, double alpha, const double* A, int64_t lda,
+          const double* B, int64_t ldb, double beta, const double* X, int64_t ldx, double gamma,
+          const double* Z, int64_t ldz, double* C, int64_t ldc) {
+  if (K >= OZ_NN_MIN_K && 2.0 * m * (double)cols * K >= OZ_MIN_FLOPS) {
+    TK_TRY(oz_split_rows(A, lda, m, K, nullptr, 0, 0, OZ_GEMM_SLICES, &e.a, e.s));
+    TK_TRY(oz_split_cols(B, ldb, K, cols, OZ_GEMM_SLICES, &e.b, e.s));
+    return oz_gemm_nt(e.a, e.b, false, alpha, beta, X, ldx, gamma, Z, ldz, C, ldc, e.status,
+                      e.s, "gemm_ozaki");
+  }
+  return gemm_nn_f64(m, cols, K, alpha, A, lda, B, ldb, beta, X, ldx, gamma, Z, ldz, C, ldc, e.s);
+}
+
 // Work arrays of cholqr2.
 struct CholWork {
   double* T;     // n x k (only for k > TRSM_MAX_K)
@@ -727,9 +798,9 @@ struct CholWork {
 
 // One pass for k > TRSM_MAX_K: explicit inverse and a GEMM (the factorisation then runs in
 // global memory on one CTA; such k occur only for very large cores).
-int cholqr_pass_inverse(double* V, int64_t ldv, int n, int k, const CholWork& w, int* stat,
-                        cudaStream_t s, bool* shifted) {
-  TK_TRY(gemm_tn_f64(k, k, n, V, ldv, V, ldv, w.Gk, k, s));
+int cholqr_pass_inverse(EigOps& e, double* V, int64_t ldv, int n, int k, const CholWork& w,
+                        int* stat, cudaStream_t s, bool* shifted) {
+  TK_TRY(op_tn(e, k, k, n, V, ldv, V, ldv, w.Gk, k));
   double shift = 0.0;
   *shifted = false;
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -753,16 +824,16 @@ int cholqr_pass_inverse(double* V, int64_t ldv, int n, int k, const CholWork& w,
     shift = 11.0 * ((double)n * k + (double)k * (k + 1)) * 2.220446049250313e-16 * tr;
     *shifted = true;
   }
-  TK_TRY(gemm_nn_f64(n, k, k, 1.0, V, ldv, w.Ri, k, 0.0, nullptr, 0, 0.0, nullptr, 0, w.T, k, s));
+  TK_TRY(op_nn(e, n, k, k, 1.0, V, ldv, w.Ri, k, 0.0, nullptr, 0, 0.0, nullptr, 0, w.T, k));
   TK_TRY(copy_cols_f64(n, k, w.T, k, V, ldv, s));
   return TUCKER_OK;
 }
 
 // One pass for k <= TRSM_MAX_K, all on the device: G = V^T V, R = chol(G) (shifted on
 // breakdown, flagged in *stat), V <- V R^{-1} by row-wise triangular solves.
-int cholqr_pass(double* V, int64_t ldv, int n, int k, const CholWork& w, int* stat,
+int cholqr_pass(EigOps& e, double* V, int64_t ldv, int n, int k, const CholWork& w, int* stat,
                 cudaStream_t s) {
-  TK_TRY(gemm_tn_f64(k, k, n, V, ldv, V, ldv, w.Gk, k, s));
+  TK_TRY(op_tn(e, k, k, n, V, ldv, V, ldv, w.Gk, k));
   {
     ProfScope prof("chol_f64", s, (double)k * k * k / 3.0, 0.0);
     static const cudaError_t attr = cudaFuncSetAttribute(
@@ -780,12 +851,12 @@ int cholqr_pass(double* V, int64_t ldv, int n, int k, const CholWork& w, int* st
 // pass whose Gram matrix is not numerically positive definite is redone with a diagonal shift
 // and does not count as clean.  Two passes are issued before the one host synchronisation that
 // reads their status words.
-int cholqr2(double* V, int64_t ldv, int n, int k, const CholWork& w, cudaStream_t s) {
+int cholqr2(EigOps& e, double* V, int64_t ldv, int n, int k, const CholWork& w, cudaStream_t s) {
   if (k > TRSM_MAX_K) {
     int clean = 0;
     for (int pass = 0; pass < 8 && clean < 2; ++pass) {
       bool shifted = false;
-      TK_TRY(cholqr_pass_inverse(V, ldv, n, k, w, w.stat, s, &shifted));
+      TK_TRY(cholqr_pass_inverse(e, V, ldv, n, k, w, w.stat, s, &shifted));
       if (!shifted) ++clean;
     }
     return clean >= 2 ? TUCKER_OK : TUCKER_EINTERNAL;
@@ -796,7 +867,7 @@ int cholqr2(double* V, int64_t ldv, int n, int k, const CholWork& w, cudaStream_
   while (clean < 2) {
     const int want = std::min(8, issued + (2 - clean));
     if (want <= issued) break;
-    for (; issued < want; ++issued) TK_TRY(cholqr_pass(V, ldv, n, k, w, w.stat + issued, s));
+    for (; issued < want; ++issued) TK_TRY(cholqr_pass(e, V, ldv, n, k, w, w.stat + issued, s));
     TK_CUDA(cudaMemcpyAsync(hs, w.stat, sizeof(int) * issued, cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
     for (; checked < issued; ++checked) {
@@ -808,11 +879,11 @@ int cholqr2(double* V, int64_t ldv, int n, int k, const CholWork& w, cudaStream_
 }
 
 // Va <- Va - L (L^T Va): the n x ka block Va (ld ldv) against nl locked columns L (ld ldl).
-int deflate(const double* L, int64_t ldl, double* Va, int64_t ldv, int n, int nl, int ka,
-            double* P, cudaStream_t s) {
+int deflate(EigOps& e, const double* L, int64_t ldl, double* Va, int64_t ldv, int n, int nl,
+            int ka, double* P) {
   if (nl <= 0 || ka <= 0) return TUCKER_OK;
-  TK_TRY(gemm_tn_f64(nl, ka, n, L, ldl, Va, ldv, P, ka, s));
-  TK_TRY(gemm_nn_f64(n, ka, nl, -1.0, L, ldl, P, ka, 1.0, Va, ldv, 0.0, nullptr, 0, Va, ldv, s));
+  TK_TRY(op_tn(e, nl, ka, n, L, ldl, Va, ldv, P, ka));
+  TK_TRY(op_nn(e, n, ka, nl, -1.0, L, ldl, P, ka, 1.0, Va, ldv, 0.0, nullptr, 0, Va, ldv));
   return TUCKER_OK;
 }
 
@@ -881,6 +952,13 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   TK_TRY(stat.alloc(sizeof(int) * 8, s));
   const CholWork cw{Tc.as<double>(), Gk.as<double>(), R.as<double>(), Ri.as<double>(),
                     rd.as<double>(), stat.as<int>()};
+  Buf ozst;
+  TK_TRY(ozst.alloc(sizeof(int), s));
+  TK_CUDA(cudaMemsetAsync(ozst.p, 0, sizeof(int), s));
+  EigOps ops;
+  ops.s = s;
+  ops.n = n;
+  ops.status = ozst.as<int>();
   double* V = Vb.as<double>();
   int c0 = 0;
   if (U0) {
@@ -890,7 +968,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   random_cols<<<ceil_div((int64_t)n * (k - c0), 256), 256, 0, s>>>(V, k, n, c0, k,
                                                                    0x5EEDull + (uint64_t)n * 131 + J);
   TK_LAUNCH();
-  TK_TRY(cholqr2(V, k, n, k, cw, s));
+  TK_TRY(cholqr2(ops, V, k, n, k, cw, s));
   // Power steps before the first Rayleigh-Ritz solve (which on a random block would buy
   // nothing): V <- orth(normalise(M V) + 1e-3 V).  The small multiple of V keeps the block of
   // full rank when M has fewer than k nonzero eigenvalues.  (A warm start with a single power
@@ -898,17 +976,15 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   const int power_steps = 4;
   for (int rep = 0; rep < power_steps; ++rep) {
     double* W = T1.as<double>();
-    if (use32)
-      TK_TRY(gemm_nn_f32a(n, k, n, 1.0, M32, n, V, k, 0.0, nullptr, 0, 0.0, nullptr, 0, W, k, s));
-    else
-      TK_TRY(gemm_nn_f64(n, k, n, 1.0, M, n, V, k, 0.0, nullptr, 0, 0.0, nullptr, 0, W, k, s));
+    TK_TRY(op_mv(ops, M, use32 ? M32 : nullptr, V, k, k, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, W,
+                 k));
     st->matvecs++;
     normalize_cols_inplace<<<k, 256, 0, s>>>(W, k, n);
     TK_LAUNCH();
     add_scaled<<<ceil_div((int64_t)n * k, 256), 256, 0, s>>>(W, V, 1e-3, (int64_t)n * k);
     TK_LAUNCH();
     TK_TRY(copy_cols_f64(n, k, W, k, V, k, s));
-    const int qs = cholqr2(V, k, n, k, cw, s);
+    const int qs = cholqr2(ops, V, k, n, k, cw, s);
     if (qs != TUCKER_OK) {
       set_error_detail("eigensolver: Cholesky-QR failed in the initial power steps");
       return qs;
@@ -928,9 +1004,9 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     double* Va = V + nl;
     double* W = T1.as<double>();
     // Rayleigh-Ritz on the active block.
-    TK_TRY(gemm_nn_f64(n, ka, n, 1.0, M, n, Va, k, 0.0, nullptr, 0, 0.0, nullptr, 0, W, ka, s));
+    TK_TRY(op_mv(ops, M, nullptr, Va, k, ka, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, W, ka));
     st->matvecs++;
-    TK_TRY(gemm_tn_f64(ka, ka, n, Va, k, W, ka, H.as<double>(), ka, s));
+    TK_TRY(op_tn(ops, ka, ka, n, Va, k, W, ka, H.as<double>(), ka));
     // Eigenpairs of H to a tenth of the locking tolerance (relative to the largest Ritz value
     // seen so far, or to |H| on the first solve).
     SyevStats ss;
@@ -940,16 +1016,22 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     st->refine_steps += ss.steps;
     st->fp64_fallbacks += ss.fallback;
     if (js != TUCKER_OK) return js;
-    TK_TRY(gemm_nn_f64(n, ka, ka, 1.0, Va, k, Qh.as<double>(), ka, 0.0, nullptr, 0, 0.0, nullptr,
-                       0, T2.as<double>(), ka, s));
-    TK_TRY(gemm_nn_f64(n, ka, ka, 1.0, W, ka, Qh.as<double>(), ka, 0.0, nullptr, 0, 0.0, nullptr,
-                       0, T3.as<double>(), ka, s));
+    TK_TRY(op_nn(ops, n, ka, ka, 1.0, Va, k, Qh.as<double>(), ka, 0.0, nullptr, 0, 0.0, nullptr,
+                 0, T2.as<double>(), ka));
+    TK_TRY(op_nn(ops, n, ka, ka, 1.0, W, ka, Qh.as<double>(), ka, 0.0, nullptr, 0, 0.0, nullptr,
+                 0, T3.as<double>(), ka));
     TK_TRY(copy_cols_f64(n, ka, T2.as<double>(), ka, Va, k, s));
     residual_norms<<<ka, 256, 0, s>>>(T3.as<double>(), T2.as<double>(), ka, n, evh, rn);
     TK_LAUNCH();
     // one copy of both (Ritz values in [0, k), residuals in [k, 2k))
     TK_CUDA(cudaMemcpyAsync(thrr.data(), evh, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
+    int ozs = 0;
+    TK_CUDA(cudaMemcpyAsync(&ozs, ozst.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     TK_CUDA(cudaStreamSynchronize(s));
+    if (ozs & DEV_TIMEOUT) {
+      set_error_detail("eigensolver: a bounded wait in a tensor-core product gave up");
+      return TUCKER_ETIMEOUT;
+    }
     theta1 = std::max(theta1, th[0]);
     const double thr = tol * std::max(theta1, 1e-300);
     int nlock = 0;
@@ -970,8 +1052,9 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
                                                                     LS.as<double>(),
                                                                     Lt.as<double>());
       TK_LAUNCH();
-      TK_TRY(gemm_nn_f64(n, n, nl, -1.0, LS.as<double>(), nl, Lt.as<double>(), n, 1.0, M, n, 0.0,
-                         nullptr, 0, Md.as<double>(), n, s));
+      TK_TRY(op_nn(ops, n, n, nl, -1.0, LS.as<double>(), nl, Lt.as<double>(), n, 1.0, M, n, 0.0,
+                   nullptr, 0, Md.as<double>(), n));
+      ops.invalidate();   // Md was rewritten: its slices must be cut again
       if (M32) TK_TRY(f64_to_f32(Md.as<double>(), Md32.as<float>(), (int64_t)n * n, s));
       Mf = Md.as<double>();
       Mf32 = M32 ? Md32.as<float>() : nullptr;
@@ -1008,29 +1091,21 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
       double* Y0 = T1.as<double>();
       double* Y1 = T2.as<double>();
       TK_TRY(copy_cols_f64(n, ka2, Xa, k, Y0, ka2, s));
-      if (use32)
-        TK_TRY(gemm_nn_f32a(n, ka2, n, 1.0 / e, Mf32, n, Y0, ka2, -cc / e, Y0, ka2, 0.0, nullptr,
-                            0, Y1, ka2, s));
-      else
-        TK_TRY(gemm_nn_f64(n, ka2, n, 1.0 / e, Mf, n, Y0, ka2, -cc / e, Y0, ka2, 0.0, nullptr, 0,
-                           Y1, ka2, s));
+      TK_TRY(op_mv(ops, Mf, use32 ? Mf32 : nullptr, Y0, ka2, ka2, 1.0 / e, -cc / e, Y0, ka2, 0.0,
+                   nullptr, 0, Y1, ka2));
       st->matvecs++;
       for (int j = 2; j <= d; ++j) {
         // Y0 <- (2/e) M Y1 - (2c/e) Y1 - Y0, then swap roles.
-        if (use32)
-          TK_TRY(gemm_nn_f32a(n, ka2, n, 2.0 / e, Mf32, n, Y1, ka2, -2.0 * cc / e, Y1, ka2, -1.0,
-                              Y0, ka2, Y0, ka2, s));
-        else
-          TK_TRY(gemm_nn_f64(n, ka2, n, 2.0 / e, Mf, n, Y1, ka2, -2.0 * cc / e, Y1, ka2, -1.0, Y0,
-                             ka2, Y0, ka2, s));
+        TK_TRY(op_mv(ops, Mf, use32 ? Mf32 : nullptr, Y1, ka2, ka2, 2.0 / e, -2.0 * cc / e, Y1,
+                     ka2, -1.0, Y0, ka2, Y0, ka2));
         st->matvecs++;
         double* t = Y0; Y0 = Y1; Y1 = t;
       }
       TK_TRY(copy_cols_f64(n, ka2, Y1, ka2, Xa, k, s));
-      for (int dd = 0; dd < 2; ++dd) TK_TRY(deflate(V, k, Xa, k, n, nl, ka2, P.as<double>(), s));
+      for (int dd = 0; dd < 2; ++dd) TK_TRY(deflate(ops, V, k, Xa, k, n, nl, ka2, P.as<double>()));
       normalize_cols_inplace<<<ka2, 256, 0, s>>>(Xa, k, n);
       TK_LAUNCH();
-      const int qs = cholqr2(Xa, k, n, ka2, cw, s);
+      const int qs = cholqr2(ops, Xa, k, n, ka2, cw, s);
       if (qs != TUCKER_OK) {
         char msg[256];
         snprintf(msg, sizeof(msg),

@@ -1,0 +1,659 @@
+// FP64-accurate matrix products on the BF16 tensor cores.  The GB300's FP64 rate is about
+// 1.25 TFLOP/s; the products of this file reach FP64 accuracy on the BF16 tensor pipe by
+// error-free splitting (the scheme of Ozaki, Ogita, Oishi and Rump, "Error-free transformations
+// of matrix multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012).  They serve the FP64 Gram of the projections
+// (the "U_(1) U_(1)^T" and slice-sum matrices of Figures hooi3, sp3, mp3) and the eigensolver's
+// products with M.
+//
+//   * every row i of an operand (a row of A, or a column of B for A B) is scaled by a power of
+//     two, u = y 2^-e_i with |u| < 1/2, and cut into S = 7 integer slices of 7 bits,
+//     u = sum_s q_s 2^(-7(s+1)) + r with |q_s| <= 64 and |r| <= 2^-50 (each q_s exact in BF16);
+//   * u_i . v_j = 2^-14 sum_d L_d 2^(-7d), with the level sums L_d = sum_{s+t=d} q_s(i).q_t(j)
+//     kept for d <= 6 (28 slice pairs); the dropped pairs and r contribute about 2^-49;
+//   * each level has its own FP32 accumulator in tensor memory.  Its products are integers of
+//     at most 2^12, so a chunk of 256 K columns (levels 0..3) or 128 (levels 4..6) sums to at
+//     most 2^22 in magnitude and the FP32 accumulation is exact;
+//   * the level chunks are read out on a staggered schedule (at most two levels per K stage,
+//     while the tensor pipe works on the others), converted to integers and summed in 64-bit
+//     integer registers: hi = sum_{d<=3} L_d 2^(7(3-d)), lo = sum_{d>=4} L_d 2^(7(6-d)).  The
+//     integer sums are exact, so the result does not depend on the order of the K chunks;
+//   * a reduction kernel adds the K splits' integer partials, scales them back to FP64 and
+//     applies the epilogue alpha C + beta X + gamma Z.
+//
+// Layout: one CTA computes a 128 x 64 tile (rows of A = tile ti of 128 rows, rows of B^T =
+// tile tj of 64 rows; for a symmetric product only tj <= 2 ti + 1, the lower triangle) over a
+// range of K stages of 32 columns.  Warp 0 streams all 7 slices of A (128 x 32) and B (64 x 32)
+// of a stage with two 3-D TMA loads (64-byte swizzle) through a 2-stage ring; warp 1 issues
+// the 56 MMAs of a stage (M = 128, N = 64, K = 16, kind::f16); warps 2-9 read the level
+// accumulators out.  Every wait is bounded: on a timeout the kernel records DEV_TIMEOUT,
+// drains and returns.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+namespace tk {
+
+namespace {
+
+constexpr int BETA = 7;                              // bits per slice
+constexpr int TM = 128, TN = 64, KS = 32, STAGES = 2;
+constexpr int NTHREADS = 320;                        // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr uint32_t IDESC = tc::idesc_bf16(TM, TN);
+
+// Ring geometry for S slices per operand (S levels, S (S + 1) / 2 slice pairs): one stage holds
+// all S slices of A (S x 8 KB) and of B (S x 4 KB); S <= 8 (8 levels x 64 columns = all of TMEM).
+template <int S>
+struct Geo {
+  static constexpr int A_BYTES = S * TM * KS * 2;
+  static constexpr int B_BYTES = S * TN * KS * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
+};
+
+// Readout schedule of level d: its accumulator restarts at local stage j > 0 when
+// j % CHUNK[d] == RESIDUE[d] (a chunk of CHUNK[d] stages of 32 columns at most).
+__host__ __device__ constexpr int level_chunk(int d) { return d <= 3 ? 8 : 4; }
+__host__ __device__ constexpr int level_residue(int d) {
+  return d == 0 ? 0 : d == 1 ? 6 : d == 2 ? 4 : d == 3 ? 2 : (d & 1) ? 3 : 1;
+}
+__device__ __forceinline__ bool restarts(int d, int j) {
+  return j > 0 && j % level_chunk(d) == level_residue(d);
+}
+
+// Grid geometry: CTA b computes tile pair b % npairs over K split b / npairs.  Tile pairs are
+// numbered row by row: (ti, tj) -> ti * ntj + tj, or for a symmetric product (tj <= 2 ti + 1,
+// every row but possibly the last has 2 ti + 2 pairs) ti (ti + 1) + tj.
+struct Grid {
+  int ntj, npairs, nsplit, nst;
+  int sym;
+};
+
+struct Job {
+  int ti, tj;   // 128-row tile of A, 64-row tile of B^T
+  int s0, ns;   // first K stage and number of stages
+};
+
+__host__ __device__ inline void pair_tiles(const Grid& g, int p, int* ti, int* tj) {
+  if (!g.sym) {
+    *ti = p / g.ntj;
+    *tj = p % g.ntj;
+    return;
+  }
+  int t = (int)((sqrt(4.0 * (double)p + 1.0) - 1.0) * 0.5);
+  while (t * (t + 1) > p) --t;
+  while ((t + 1) * (t + 2) <= p) ++t;
+  *ti = t;
+  *tj = p - t * (t + 1);
+}
+
+__host__ __device__ inline int pair_index(const Grid& g, int ti, int tj) {
+  return g.sym ? ti * (ti + 1) + tj : ti * g.ntj + tj;
+}
+
+__device__ inline Job job_of(const Grid& g, int b) {
+  Job j;
+  const int z = b / g.npairs, p = b % g.npairs;
+  pair_tiles(g, p, &j.ti, &j.tj);
+  j.s0 = (int)((int64_t)g.nst * z / g.nsplit);
+  j.ns = (int)((int64_t)g.nst * (z + 1) / g.nsplit) - j.s0;
+  return j;
+}
+
+template <int S>
+__global__ void __launch_bounds__(NTHREADS, 1)
+gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const Grid grid, long long* __restrict__ partial, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * Geo<S>::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;   // [S] a level's chunk is complete in TMEM
+  uint64_t* acc_free = acc_full + S;     // [S] the epilogue has read it
+  uint64_t* done = acc_free + S;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Job job = job_of(grid, blockIdx.x);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int d = 0; d < S; ++d) {
+      tc::mbar_init(&acc_full[d], 1);
+      tc::mbar_init(&acc_free[d], 8);   // one arrival per epilogue warp
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: all slices of A and B for one K stage per ring slot ------------------
+    int issued = 0;
+    for (int j = 0; j < job.ns; ++j) {
+      const int s = j % STAGES;
+      if (j >= STAGES && !tc::mbar_wait(&empty[s], ((j / STAGES) - 1) & 1, status, abort_flag))
+        break;
+      uint8_t* st = smem + s * Geo<S>::STAGE_BYTES;
+      tc::mbar_expect_tx(&full[s], Geo<S>::STAGE_BYTES);
+      const int kx = (job.s0 + j) * KS;
+      tc::tma_load_3d(st, &mapA, &full[s], kx, job.ti * TM, 0);
+      tc::tma_load_3d(st + Geo<S>::A_BYTES, &mapB, &full[s], kx, job.tj * TN, 0);
+      ++issued;
+    }
+    if (*abort_flag)
+      for (int j = issued > STAGES ? issued - STAGES : 0; j < issued; ++j)
+        tc::mbar_drain(&full[j % STAGES], (j / STAGES) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----------------------------------------------------------------------------
+    uint32_t free_phase = 0;   // bit d: parity of the next acc_free[d] phase to wait for
+    bool ok = true;
+    for (int j = 0; j < job.ns && ok; ++j) {
+      const int s = j % STAGES;
+      if (!tc::mbar_wait(&full[s], (j / STAGES) & 1, status, abort_flag)) break;
+      tc::fence_after();
+      const uint8_t* st = smem + s * Geo<S>::STAGE_BYTES;
+      // Slice q of A (B) starts q * 8 KB (4 KB) after slice 0: descriptor address field + q *
+      // bytes / 16 (the whole ring lies below 256 KB, so the 14-bit field does not overflow).
+      const uint64_t da0 = tc::sw_desc(st, 64), db0 = tc::sw_desc(st + Geo<S>::A_BYTES, 64);
+      constexpr uint64_t DA = (TM * KS * 2) >> 4, DB = (TN * KS * 2) >> 4;
+      // Levels that keep accumulating first, then the restarting ones (their accumulators
+      // must first have been read out).
+      for (int pass = 0; pass < 2 && ok; ++pass) {
+        for (int d = 0; d < S; ++d) {
+          const bool rs = restarts(d, j);
+          if ((pass == 0) == rs) continue;
+          if (rs) {
+            if (!tc::mbar_wait(&acc_free[d], (free_phase >> d) & 1u, status, abort_flag)) {
+              ok = false;
+              break;
+            }
+            free_phase ^= 1u << d;
+            tc::fence_after();
+          }
+          const uint32_t dt = tmem + (uint32_t)(d * TN);
+          const bool fresh = (j == 0) || rs;
+#pragma unroll
+          for (int kk = 0; kk < KS / 16; ++kk) {
+            const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
+            for (int q = 0; q <= d; ++q)
+              tc::mma_bf16<IDESC>(dt, da0 + q * DA + off, db0 + (d - q) * DB + off,
+                                  (fresh && kk == 0 && q == 0) ? 0u : 1u);
+          }
+        }
+      }
+      if (!ok) break;
+      tc::mma_commit(&empty[s]);
+      const bool last = j + 1 == job.ns;
+      for (int d = 0; d < S; ++d)
+        if (last || restarts(d, j + 1)) tc::mma_commit(&acc_full[d]);
+    }
+    tc::mma_commit(done);   // arrives once every MMA issued above has completed
+  } else if (warp >= 2) {
+    // ---- epilogue: level readouts into exact 64-bit integer sums -----------------------------
+    const int q = warp & 3;              // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;       // column half of the 64-column level accumulator
+    long long hi[32], lo[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0;
+    uint32_t full_phase = 0;   // bit d: parity of the next acc_full[d] phase to wait for
+    bool ok = true;
+    auto readout = [&](int d) {
+      if (!ok) return;
+      if (!tc::mbar_wait(&acc_full[d], (full_phase >> d) & 1u, status, abort_flag)) {
+        ok = false;
+        return;
+      }
+      full_phase ^= 1u << d;
+      tc::fence_after();
+      uint32_t r[32];
+      tc::tmem_ld32_raw(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * TN + h * 32), r);
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acc_free[d]);
+      // |L| <= 2^22: adding 1.5 * 2^23 puts the integer in the low mantissa bits.
+      const int sh = d <= 3 ? BETA * (3 - d) : BETA * (S - 1 - d);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int v = __float_as_int(__uint_as_float(r[i]) + 12582912.0f) - 0x4B400000;
+        const long long w = (long long)v << sh;
+        if (d <= 3)
+          hi[i] += w;
+        else
+          lo[i] += w;
+      }
+    };
+    for (int j = 1; j < job.ns && ok; ++j)
+      for (int d = 0; d < S; ++d)
+        if (restarts(d, j)) readout(d);
+    if (job.ns > 0)
+      for (int d = 0; d < S; ++d) readout(d);
+    if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
+      const int row = q * 32 + lane;
+      long long* ph = partial + (int64_t)blockIdx.x * 2 * TM * TN + (int64_t)row * TN + h * 32;
+      long long* pl = ph + TM * TN;
+#pragma unroll
+      for (int i = 0; i < 32; i += 2) {
+        *reinterpret_cast<longlong2*>(ph + i) = make_longlong2(hi[i], hi[i + 1]);
+        *reinterpret_cast<longlong2*>(pl + i) = make_longlong2(lo[i], lo[i + 1]);
+      }
+    }
+  }
+  __syncwarp();
+  // Nobody frees tensor memory while MMAs may still be in flight.
+  if (!tc::mbar_wait(done, 0, status, abort_flag)) tc::mbar_drain(done, 0);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+// The splitting runs in integer arithmetic on the FP64 bit patterns (this part's FP64 pipe
+// is far too slow for it).  A row's scale exponent e satisfies |y 2^-e| < 1/2 for every y in
+// the row: e = frexp exponent of max |y| + 1, computed from the largest |y| bit pattern (for
+// non-negative doubles the bit patterns order like the values).  A zero row gets OZ_ZERO_EXP
+// (its slices are zero, and two such exponents still add without overflow).
+constexpr int OZ_ZERO_EXP = -1100;
+__device__ __forceinline__ int oz_exponent_bits(unsigned long long a) {
+  if (a == 0ull) return OZ_ZERO_EXP;
+  const int be = (int)(a >> 52);
+  if (be > 0) return be - 1021;                 // a = 1.f 2^(be - 1023): frexp exponent be - 1022
+  return (63 - __clzll((long long)a)) - 1072;   // subnormal
+}
+__device__ __forceinline__ unsigned long long abs_bits(double y) {
+  return (unsigned long long)__double_as_longlong(y) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Z = round(y 2^(7 S - e)) as a signed integer; |Z| <= 2^(7 S - 1) when |y| < 2^(e-1).
+template <int S>
+__device__ __forceinline__ long long oz_fixed(double y, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const int be = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (be > 0) m |= 1ull << 52;
+  if (m == 0ull) return 0;
+  const int sh = (be > 0 ? be - 1075 : -1074) + BETA * S - e;   // Z = m 2^sh
+  long long z;
+  if (sh >= 0)
+    z = (long long)(m << sh);                      // subnormal rows only; still below 2^55
+  else if (sh > -64)
+    z = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+  else
+    z = 0;
+  return (b >> 63) ? -z : z;
+}
+
+// Cuts Z into S balanced base-128 digits, Z = sum_s q_s 128^(S-1-s) with q_(S-1)..q_1 in
+// [-64, 63] and |q_0| <= 64, and stores slice s (q_s as a BF16 integer) at out[s * plane].
+template <int S>
+__device__ __forceinline__ void oz_cut(long long z, __nv_bfloat16* out, int64_t plane) {
+  int q[S];
+#pragma unroll
+  for (int s = S - 1; s > 0; --s) {
+    const int d = (int)((z + 64) & 127) - 64;
+    q[s] = d;
+    z = (z - d) >> 7;                             // exact: z - d is a multiple of 128
+  }
+  q[0] = (int)z;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    __nv_bfloat16_raw r;
+    r.x = (unsigned short)(__float_as_uint((float)q[s]) >> 16);   // exact: at most 7 bits
+    out[s * plane] = r;
+  }
+}
+
+// Row exponents of [A | A2] (A: rows x K1, ld lda; A2: rows x K2, ld lda2): one block per row.
+__global__ void oz_scale_rows(const double* __restrict__ A, int64_t lda, int64_t K1,
+                              const double* __restrict__ A2, int64_t lda2, int64_t K2,
+                              int* __restrict__ ex) {
+  __shared__ unsigned long long ws[8];
+  const int r = blockIdx.x;
+  unsigned long long m = 0ull;
+  for (int64_t k = threadIdx.x; k < K1; k += blockDim.x) {
+    const unsigned long long a = abs_bits(A[(int64_t)r * lda + k]);
+    m = a > m ? a : m;
+  }
+  for (int64_t k = threadIdx.x; k < K2; k += blockDim.x) {
+    const unsigned long long a = abs_bits(A2[(int64_t)r * lda2 + k]);
+    m = a > m ? a : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t > m ? t : m;
+  }
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0ull;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = ws[w] > t ? ws[w] : t;
+    ex[r] = oz_exponent_bits(t);
+  }
+}
+
+// Slices of the rows of [A | A2]: Q[s][r][k], r < rows_pad, k < ldK; columns [0, K1) from A,
+// [K1p, K1p + K2) from A2 (K1p = K1 rounded up to a stage), zero elsewhere.  Each thread cuts
+// 4 consecutive columns.
+template <int S>
+__global__ void oz_split_rows_kernel(int rows, int rows_pad, const double* __restrict__ A,
+                                     int64_t lda, int64_t K1, int64_t K1p,
+                                     const double* __restrict__ A2, int64_t lda2, int64_t K2,
+                                     int64_t ldK, const int* __restrict__ ex,
+                                     __nv_bfloat16* __restrict__ Q) {
+  const int64_t quads = ldK / 4;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)rows_pad * quads) return;
+  const int r = (int)(t / quads);
+  const int64_t k0 = (t % quads) * 4;
+  const int e = r < rows ? ex[r] : 0;
+  const int64_t plane = (int64_t)rows_pad * ldK;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t k = k0 + i;
+    double y = 0.0;
+    if (r < rows) {
+      if (k < K1)
+        y = A[(int64_t)r * lda + k];
+      else if (k >= K1p && k - K1p < K2)
+        y = A2[(int64_t)r * lda2 + (k - K1p)];
+    }
+    oz_cut<S>(oz_fixed<S>(y, e), Q + (int64_t)r * ldK + k, plane);
+  }
+}
+
+// Column exponents of B (K x cols, ld ldb): blocks of 32 columns x 256 rows, combined with
+// atomicMax (ex starts at INT_MIN).
+__global__ void oz_scale_cols(const double* __restrict__ B, int64_t ldb, int64_t K, int cols,
+                              int* __restrict__ ex) {
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.y * 256;
+  unsigned long long m = 0ull;
+  if (c < cols)
+    for (int64_t k = k0 + threadIdx.y; k < K && k < k0 + 256; k += 8) {
+      const unsigned long long a = abs_bits(B[k * ldb + c]);
+      m = a > m ? a : m;
+    }
+  if (c < cols && m != 0ull) atomicMax(&ex[c], oz_exponent_bits(m));
+}
+
+__global__ void oz_fix_zero_cols(int cols, int* __restrict__ ex) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cols && ex[c] < OZ_ZERO_EXP) ex[c] = OZ_ZERO_EXP;
+}
+
+// Slices of the columns of B (K x cols, ld ldb), i.e. of the rows of B^T: Q[s][c][k] for
+// c < rows_pad, k < ldK, through a 32 x 32 shared-memory transpose.
+template <int S>
+__global__ void oz_split_cols_kernel(const double* __restrict__ B, int64_t ldb, int64_t K,
+                                     int cols, int rows_pad, int64_t ldK,
+                                     const int* __restrict__ ex, __nv_bfloat16* __restrict__ Q) {
+  __shared__ double tile[32][33];
+  const int c0 = blockIdx.x * 32;
+  const int64_t k0 = (int64_t)blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t k = k0 + i;
+    const int c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (k < K && c < cols) ? B[k * ldb + c] : 0.0;
+  }
+  __syncthreads();
+  const int64_t plane = (int64_t)rows_pad * ldK;
+  const int64_t k = k0 + threadIdx.x;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i;
+    const int e = c < cols ? ex[c] : 0;
+    oz_cut<S>(oz_fixed<S>(tile[threadIdx.x][i], e), Q + (int64_t)c * ldK + k, plane);
+  }
+}
+
+// C[r][c] = alpha 2^(e_r + f_c - 14) (hi 2^-21 + lo 2^-7(S-1)) + beta X[r][c] + gamma Z[r][c],
+// with hi and lo summed over the K splits in integers.  A symmetric product fills r >= c and
+// mirrors.
+__global__ void oz_reduce(const long long* __restrict__ partial, const Grid g, int nslice, int m,
+                          int n,
+                          const int* __restrict__ exA, const int* __restrict__ exB, double alpha,
+                          double beta, const double* X, int64_t ldx, double gamma, const double* Z,
+                          int64_t ldz, double* C, int64_t ldc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * n) return;
+  const int r = (int)(t / n), c = (int)(t % n);
+  if (g.sym && c > r) return;
+  const int ti = r / TM, tj = c / TN;
+  const int p = pair_index(g, ti, tj);
+  const int rr = r - ti * TM, cc = c - tj * TN;
+  long long hi = 0, lo = 0;
+  for (int z = 0; z < g.nsplit; ++z) {
+    const long long* P = partial + ((int64_t)z * g.npairs + p) * 2 * TM * TN;
+    hi += P[rr * TN + cc];
+    lo += P[TM * TN + rr * TN + cc];
+  }
+  const int E = exA[r] + exB[c] - 2 * BETA;
+  double v = alpha * (ldexp((double)hi, E - 3 * BETA) +
+                      ldexp((double)lo, E - (nslice - 1) * BETA));
+  if (X) v += beta * X[(int64_t)r * ldx + c];
+  if (Z) v += gamma * Z[(int64_t)r * ldz + c];
+  C[(int64_t)r * ldc + c] = v;
+  if (g.sym) C[(int64_t)c * ldc + r] = v;
+}
+
+__global__ void zero_f64(double* __restrict__ M, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) M[t] = 0.0;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 3-D map over the slice planes: (k, row, slice), box (32, box_rows, 7), 64-byte swizzle.
+int make_slice_map(CUtensorMap* m, const OzSlices& S, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) {
+    set_error_detail("cuTensorMapEncodeTiled is not available from the driver");
+    return TUCKER_ECUDA;
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)S.ldK, (cuuint64_t)S.rows_pad, (cuuint64_t)S.nslice};
+  cuuint64_t strides[2] = {(cuuint64_t)S.ldK * 2, (cuuint64_t)S.rows_pad * (cuuint64_t)S.ldK * 2};
+  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)box_rows, (cuuint32_t)S.nslice};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S.Q.p, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error_detail("cuTensorMapEncodeTiled rejected the slice layout of an FP64 product");
+    return TUCKER_ECUDA;
+  }
+  return TUCKER_OK;
+}
+
+int reserve(OzSlices* out, int rows, int64_t ldK, int nslice, cudaStream_t s) {
+  if (nslice != 7 && nslice != 8) return TUCKER_EINVAL;
+  out->nslice = nslice;
+  out->rows = rows;
+  out->rows_pad = ceil_div(rows, TM) * TM;
+  out->ldK = ldK;
+  const size_t qb = sizeof(__nv_bfloat16) * nslice * (size_t)out->rows_pad * (size_t)ldK;
+  if (out->Q.bytes < qb || out->Q.s != s) TK_TRY(out->Q.alloc(qb, s));
+  if (out->ex.bytes < sizeof(int) * out->rows_pad || out->ex.s != s)
+    TK_TRY(out->ex.alloc(sizeof(int) * out->rows_pad, s));
+  return TUCKER_OK;
+}
+
+}  // namespace
+
+int64_t oz_ldk(int64_t K) { return (K + KS - 1) / KS * KS; }
+
+int oz_split_rows(const double* A, int64_t lda, int rows, int64_t K1, const double* A2,
+                  int64_t lda2, int64_t K2, int nslice, OzSlices* out, cudaStream_t s) {
+  if (rows < 1 || K1 < 0 || K2 < 0) return TUCKER_EINVAL;
+  if (!A2) K2 = 0;
+  const int64_t K1p = oz_ldk(K1);
+  TK_TRY(reserve(out, rows, K1p + oz_ldk(K2), nslice, s));
+  ProfScope prof("ozaki_split", s, 0.0,
+                 8.0 * rows * (double)(K1 + K2) * 2 +
+                     2.0 * nslice * out->rows_pad * (double)out->ldK);
+  oz_scale_rows<<<rows, 256, 0, s>>>(A, lda, K1, A2, lda2, K2, out->ex.as<int>());
+  TK_LAUNCH();
+  if (out->ldK == 0) return TUCKER_OK;   // no columns: nothing to cut
+  const int64_t quads = (int64_t)out->rows_pad * (out->ldK / 4);
+  auto kern = nslice == 8 ? oz_split_rows_kernel<8> : oz_split_rows_kernel<7>;
+  kern<<<ceil_div(quads, 256), 256, 0, s>>>(rows, out->rows_pad, A, lda, K1, K1p, A2, lda2, K2,
+                                            out->ldK, out->ex.as<int>(),
+                                            out->Q.as<__nv_bfloat16>());
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+int oz_split_cols(const double* B, int64_t ldb, int64_t K, int cols, int nslice, OzSlices* out,
+                  cudaStream_t s) {
+  if (cols < 1 || K < 0) return TUCKER_EINVAL;
+  TK_TRY(reserve(out, cols, oz_ldk(K), nslice, s));
+  ProfScope prof("ozaki_split", s, 0.0,
+                 8.0 * cols * (double)K * 2 + 2.0 * nslice * out->rows_pad * (double)out->ldK);
+  TK_CUDA(cudaMemsetAsync(out->ex.p, 0x80, sizeof(int) * cols, s));   // INT_MIN-like start
+  if (K > 0) {
+    oz_scale_cols<<<dim3(ceil_div(cols, 32), ceil_div(K, 256)), dim3(32, 8), 0, s>>>(
+        B, ldb, K, cols, out->ex.as<int>());
+    TK_LAUNCH();
+  }
+  oz_fix_zero_cols<<<ceil_div(cols, 256), 256, 0, s>>>(cols, out->ex.as<int>());
+  TK_LAUNCH();
+  if (out->ldK == 0) return TUCKER_OK;   // no rows of B: nothing to cut
+  auto kern = nslice == 8 ? oz_split_cols_kernel<8> : oz_split_cols_kernel<7>;
+  kern<<<dim3(out->rows_pad / 32, (unsigned)(out->ldK / 32)), dim3(32, 8), 0, s>>>(
+      B, ldb, K, cols, out->rows_pad, out->ldK, out->ex.as<int>(), out->Q.as<__nv_bfloat16>());
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+namespace {
+
+template <int S>
+int launch_products(const CUtensorMap& mapA, const CUtensorMap& mapB, const Grid& g,
+                    int64_t njobs, long long* part, int* status, cudaStream_t s) {
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      gram_ozaki_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<S>::SMEM_BYTES);
+  TK_CUDA(attr);
+  gram_ozaki_kernel<S><<<(unsigned)njobs, NTHREADS, Geo<S>::SMEM_BYTES, s>>>(mapA, mapB, g, part,
+                                                                             status);
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+}  // namespace
+
+int oz_gemm_nt(const OzSlices& A, const OzSlices& B, bool sym, double alpha, double beta,
+               const double* X, int64_t ldx, double gamma, const double* Z, int64_t ldz,
+               double* C, int64_t ldc, int* status, cudaStream_t s, const char* prof_name) {
+  if (A.ldK != B.ldK || A.nslice != B.nslice || (sym && &A != &B)) return TUCKER_EINVAL;
+  const int S = A.nslice;
+  const int m = A.rows, n = B.rows;
+  const int nti = ceil_div(m, TM), ntj = ceil_div(n, TN);
+  const int nst = (int)(A.ldK / KS);
+  Grid g{ntj, 0, 1, nst, sym ? 1 : 0};
+  g.npairs = sym ? nti * (nti + 1) - (ntj < 2 * nti ? 1 : 0) : nti * ntj;
+  // K splits: the fewest that fill the SMs' waves to 90 %, each at least 8 stages long.
+  const int sms = num_sms();
+  const int max_split = std::max(1, std::min(64, nst / 8));
+  double best = 0.0;
+  for (int z = 1; z <= max_split; ++z) {
+    const int64_t jobs = (int64_t)g.npairs * z;
+    const double eff = (double)jobs / (double)(((jobs + sms - 1) / sms) * sms);
+    if (eff > best + 1e-9) {
+      best = eff;
+      g.nsplit = z;
+    }
+    if (eff >= 0.9) break;
+  }
+  const int64_t njobs = (int64_t)g.npairs * g.nsplit;
+  if (nst == 0) {
+    // empty K: C = beta X + gamma Z
+    Buf zero;
+    TK_TRY(zero.alloc(sizeof(long long) * 2 * TM * TN * (size_t)std::max<int64_t>(njobs, 1), s));
+    TK_CUDA(cudaMemsetAsync(zero.p, 0, zero.bytes, s));
+    g.nsplit = 1;
+    oz_reduce<<<ceil_div((int64_t)m * n, 256), 256, 0, s>>>(zero.as<long long>(), g, S, m, n,
+                                                             A.ex.as<int>(), B.ex.as<int>(), alpha,
+                                                             beta, X, ldx, gamma, Z, ldz, C, ldc);
+    TK_LAUNCH();
+    return TUCKER_OK;
+  }
+  CUtensorMap mapA, mapB;
+  TK_TRY(make_slice_map(&mapA, A, TM));
+  TK_TRY(make_slice_map(&mapB, B, TN));
+  Buf part;
+  TK_TRY(part.alloc(sizeof(long long) * 2 * TM * TN * (size_t)njobs, s));
+  {
+    // flops: the BF16 tensor-core FLOPs issued (S (S + 1) / 2 slice pairs per output tile and
+    // K column); bytes: the slices read once plus the integer partials written.
+    ProfScope pk(prof_name, s, 2.0 * (S * (S + 1) / 2) * TM * TN * (double)KS * nst * g.npairs,
+                 2.0 * S * ((double)A.rows_pad + (sym ? 0.0 : (double)B.rows_pad)) * A.ldK +
+                     16.0 * TM * TN * (double)njobs);
+    if (S == 8)
+      TK_TRY(launch_products<8>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
+    else
+      TK_TRY(launch_products<7>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
+  }
+  oz_reduce<<<ceil_div((int64_t)m * n, 256), 256, 0, s>>>(part.as<long long>(), g, S, m, n,
+                                                           A.ex.as<int>(), B.ex.as<int>(), alpha,
+                                                           beta, X, ldx, gamma, Z, ldz, C, ldc);
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+int gram_f64_tc(int rows, const double* Y1, int64_t K1, const double* Y2, int64_t K2, double* M,
+                cudaStream_t s) {
+  if (rows <= 0) return TUCKER_OK;
+  if (!Y2) K2 = 0;
+  const int64_t Ktot = K1 + K2;
+  ProfScope prof("gram_f64_tc", s, (double)rows * (rows + 1) * (double)Ktot,
+                 8.0 * rows * (double)Ktot + 8.0 * rows * rows);
+  const int64_t cells = (int64_t)rows * rows;
+  if (Ktot == 0) {
+    zero_f64<<<ceil_div(cells, 256), 256, 0, s>>>(M, cells);
+    TK_LAUNCH();
+    return TUCKER_OK;
+  }
+  OzSlices S;
+  TK_TRY(oz_split_rows(Y1, K1, rows, K1, Y2, K2, K2, OZ_GRAM_SLICES, &S, s));
+  Buf st;
+  TK_TRY(st.alloc(sizeof(int), s));
+  TK_CUDA(cudaMemsetAsync(st.p, 0, sizeof(int), s));
+  TK_TRY(oz_gemm_nt(S, S, true, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, M, rows, st.as<int>(), s,
+                    "gram_ozaki"));
+  int h = 0;
+  TK_CUDA(cudaMemcpyAsync(&h, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  if (h & DEV_TIMEOUT) {
+    set_error_detail("FP64 tensor-core Gram: a bounded wait on an mbarrier gave up");
+    return TUCKER_ETIMEOUT;
+  }
+  return TUCKER_OK;
+}
+
+}  // namespace tk

@@ -49,6 +49,9 @@ int build_canonical(tucker_tensor_s* X, const int32_t* d_i0, const int32_t* d_i1
                     const int32_t* d_i2, const double* d_v, int64_t nnz_in, cudaStream_t s);
 int build_ordering(tucker_tensor_s* X, Ordering* ord, cudaStream_t s);
 int sum_squares(const double* d_v, int64_t n, double* d_out, cudaStream_t s);
+// Exclusive prefix sum of n unsigned values (in may equal out); *d_total (device) gets the sum.
+int exclusive_scan_u32(const unsigned* in, unsigned* out, int64_t n, unsigned* d_total,
+                       cudaStream_t s);
 int build_fiber_map(tucker_tensor_s* X, Ordering* ord, cudaStream_t s);
 
 // sparse.cu (FP64)
@@ -93,6 +96,36 @@ int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int
                int64_t ldY, float* Y32, cudaStream_t s);
 int slice_proj_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int64_t ldm,
                      int Jm, __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, cudaStream_t s);
+
+// gram_ozaki.cu: FP64-accurate products on the BF16 tensor cores (error-free 7-slice splitting,
+// exact integer level sums).  An operand is first cut into OzSlices: seven BF16 planes of a
+// K-major (rows_pad x ldK) matrix and one scale exponent per row.
+// nslice = 7 keeps 49 bits of every row's largest entry (error about 2^-49 max|a_i| max|b_j| per
+// term); nslice = 8 keeps 56 bits, for products whose rows are dominated by one entry and whose
+// small terms must stay accurate (the eigensolver's M V: M is strongly diagonal-dominant).
+struct OzSlices {
+  Buf Q, ex;
+  int nslice = 7;
+  int rows = 0, rows_pad = 0;
+  int64_t ldK = 0;
+};
+constexpr int OZ_GRAM_SLICES = 7, OZ_GEMM_SLICES = 8;
+int64_t oz_ldk(int64_t K);
+// Slices of the rows of [A | A2] (A: rows x K1, ld lda; A2 optional: rows x K2, ld lda2).
+int oz_split_rows(const double* A, int64_t lda, int rows, int64_t K1, const double* A2,
+                  int64_t lda2, int64_t K2, int nslice, OzSlices* out, cudaStream_t s);
+// Slices of the columns of B (K x cols, ld ldb), i.e. of the rows of B^T.
+int oz_split_cols(const double* B, int64_t ldb, int64_t K, int cols, int nslice, OzSlices* out,
+                  cudaStream_t s);
+// C (A.rows x B.rows, ld ldc) = alpha A B^T + beta X + gamma Z (X, Z optional; Z may alias C).
+// sym: B is A, only the lower triangle is computed and it is mirrored (X, Z must be NULL or
+// symmetric).  Timeouts set DEV_TIMEOUT in *status (device); prof_name names the profile record.
+int oz_gemm_nt(const OzSlices& A, const OzSlices& B, bool sym, double alpha, double beta,
+               const double* X, int64_t ldx, double gamma, const double* Z, int64_t ldz,
+               double* C, int64_t ldc, int* status, cudaStream_t s, const char* prof_name);
+// M = Y1 Y1^T (+ Y2 Y2^T), FP64-accurate; same arguments and result as syrk_f64.
+int gram_f64_tc(int rows, const double* Y1, int64_t K1, const double* Y2, int64_t K2, double* M,
+                cudaStream_t s);
 
 // gram_tc.cu: M = sum_t Y_t Y_t^T on tcgen05 with Y_t = hi + lo (BF16x3), FP64 result.
 struct GramTerm {
@@ -157,6 +190,11 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
                  double tol = EIG_TOL_FP64);
 
 // core / fit (api.cu)
+// dst (rows x cols, row-major) = src with every column scaled to unit length (zero columns
+// stay zero): the random start of Figures sp3 and sp4.
+int normalize_columns(const double* src, int rows, int cols, double* dst, cudaStream_t s);
+// *fit_dev = 1 - sqrt(max(0, nX2 - *g2_dev)) / sqrt(nX2) (fit equation, norm identity).
+int fit_on_device(double nX2, const double* g2_dev, double* fit_dev, cudaStream_t s);
 int core_from_ttmc3(const double* Y3, int I3, int J1, int J2, const double* C, int J3,
                     double* G, double* g2_dev, cudaStream_t s);
 

@@ -259,4 +259,41 @@ int unfolding_gram_f64(const tucker_tensor_s* X, const Ordering* rows, const Ord
   return h ? TUCKER_EINTERNAL : TUCKER_OK;
 }
 
+int slice_proj_f64_fibers(int64_t F, const int32_t* row, const int32_t* col,
+                          const int64_t* fiber_ptr, const int32_t* leaf_idx, const double* val,
+                          const double* Um, int Jm, int64_t ncol, double* Y, cudaStream_t s) {
+  if (F == 0) return TUCKER_OK;
+  const int64_t wpb = 8;
+  const int blocks = (int)min64((F + wpb - 1) / wpb, (int64_t)num_sms() * 64);
+  const int np = Jm <= 32 ? 1 : (Jm <= 64 ? 2 : (Jm <= 128 ? 4 : 8));
+#define TK_SP(N)                                                                              \
+  if (np == N)                                                                                \
+    slice_proj_f64_kernel<N><<<blocks, 256, 0, s>>>(F, row, col, fiber_ptr, leaf_idx, val, Um, \
+                                                    Jm, ncol, Y);
+  TK_SP(1) TK_SP(2) TK_SP(4) TK_SP(8)
+#undef TK_SP
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+int ttmc_f64_roots(int64_t nroots, const int64_t* root_ptr, const int32_t* fiber_idx,
+                   const int64_t* fiber_ptr, const int32_t* leaf_idx, const double* val,
+                   const double* Um, int Jm, const double* Uo, int Jo, double* Y, cudaStream_t s) {
+  if (nroots == 0) return TUCKER_OK;
+  const int cp = tile_code(Jm), cq = tile_code(Jo);
+  dim3 grid((unsigned)nroots, 0, 0);
+#define TK_TT(AP, AQ)                                                                          \
+  if (cp == AP && cq == AQ) {                                                                  \
+    dim3 g((unsigned)nroots, ceil_div(Jm, 16 * AP), ceil_div(Jo, 16 * AQ));                    \
+    ttmc_f64_kernel<AP, AQ><<<g, 256, 0, s>>>(root_ptr, fiber_idx, fiber_ptr, leaf_idx, val,   \
+                                              Um, Jm, Uo, Jo, Y);                              \
+  }
+  TK_TT(1, 1) TK_TT(1, 2) TK_TT(1, 4) TK_TT(2, 1) TK_TT(2, 2) TK_TT(2, 4) TK_TT(4, 1)
+  TK_TT(4, 2) TK_TT(4, 4)
+#undef TK_TT
+  (void)grid;
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
 }  // namespace tk

@@ -40,6 +40,23 @@ class tucker_result(Structure):
                 ("rank_deficient", c_int32)]
 
 
+class tucker4_coo(Structure):
+    _fields_ = [("dims", c_int64 * 4), ("nnz", c_int64), ("idx", c_void_p * 4),
+                ("val", c_void_p), ("where", c_int32)]
+
+
+class tucker4_opts(Structure):
+    _fields_ = [("precision", c_int32), ("tol", c_double), ("max_iter", c_int32),
+                ("init", c_void_p * 4), ("init_where", c_int32), ("stream", c_void_p),
+                ("flags", c_uint32)]
+
+
+class tucker4_result(Structure):
+    _fields_ = [("G", c_void_p), ("U", c_void_p * 4), ("fit_history", c_void_p),
+                ("where", c_int32), ("fit", c_double), ("iters", c_int32),
+                ("rank_deficient", c_int32)]
+
+
 class TuckerError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -64,6 +81,19 @@ _SIGS = {
                                       POINTER(tucker_result)]),
     "tucker_mp_batched": (c_int32, [c_int32, c_void_p, POINTER(c_int32), POINTER(tucker_opts),
                                     POINTER(tucker_result)]),
+    "tucker4_tensor_create": (c_int32, [POINTER(tucker4_coo), c_void_p, POINTER(c_void_p)]),
+    "tucker4_tensor_destroy": (c_int32, [c_void_p]),
+    "tucker4_tensor_info": (c_int32, [c_void_p, POINTER(c_int64), POINTER(c_double)]),
+    "tucker4_hosvd": (c_int32, [c_void_p, POINTER(c_int32), POINTER(tucker4_opts),
+                                POINTER(tucker4_result)]),
+    "tucker4_hooi": (c_int32, [c_void_p, POINTER(c_int32), POINTER(tucker4_opts),
+                               POINTER(tucker4_result)]),
+    "tucker4_sp": (c_int32, [c_void_p, POINTER(c_int32), POINTER(tucker4_opts),
+                             POINTER(tucker4_result)]),
+    "tucker4_mp": (c_int32, [c_void_p, POINTER(c_int32), POINTER(tucker4_opts),
+                             POINTER(tucker4_result)]),
+    "tucker4_ttmc": (c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_int32), c_void_p,
+                               c_void_p]),
     "tucker_strerror": (c_char_p, [c_int32]),
     "tucker_last_error_detail": (c_char_p, []),
     "tucker_ordering": (c_int32, [c_void_p, c_int32, c_int32, c_int32, POINTER(c_int64), c_void_p,
@@ -84,6 +114,8 @@ _SIGS = {
                                           c_void_p, c_void_p, c_int64, c_void_p]),
     "tucker_gram_bf16x3": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p,
                                      c_int64, c_int64, c_int32, c_void_p, c_void_p]),
+    "tucker_gemm": (c_int32, [c_void_p, c_int64, c_void_p, c_int64, c_int32, c_int32, c_int64,
+                              c_void_p, c_int64, c_void_p]),
     "tucker_gram_noalloc": (c_int32, [c_void_p, c_int64, c_void_p, c_int64, c_int32, c_void_p,
                                       c_void_p]),
     "tucker_profile_enable": (None, [c_int32]),
@@ -275,8 +307,8 @@ def tucker_sp(X: Tensor, J, C_raw, tol=1e-4, max_iter=50, precision="fp64", out=
     return _run("tucker_sp", X, J, precision, tol, max_iter, [None, None, C_raw], out)
 
 
-def tucker_mp(X: Tensor, J, tol=1e-4, max_iter=50, precision="fp64", out="device"):
-    return _run("tucker_mp", X, J, precision, tol, max_iter, None, out)
+def tucker_mp(X: Tensor, J, tol=1e-4, max_iter=50, precision="fp64", init=None, out="device"):
+    return _run("tucker_mp", X, J, precision, tol, max_iter, init, out)
 
 
 def _run_batched(fn_name, Xs, Js, precision, tol, max_iter):
@@ -316,12 +348,15 @@ def tucker_mp_batched(Xs, Js, tol=1e-4, max_iter=50, precision="fp64"):
 
 # ---- step entry points -------------------------------------------------------------------------
 
-def tucker_ordering(X: Tensor, n, m, o):
-    """Copies ordering (n, m, o) to host numpy arrays."""
+def tucker_ordering(X: Tensor, n, m, o, copy=True):
+    """Builds ordering (n, m, o) if needed and copies it to host numpy arrays; with copy=False
+    only builds it and returns its fiber count."""
     lib = _lib()
     F = c_int64()
     _check(lib.tucker_ordering(X.handle, n, m, o, ctypes.byref(F), None, None, None, None, None,
                                TUCKER_HOST), "tucker_ordering")
+    if not copy:
+        return int(F.value)
     nnz, _ = tucker_tensor_info(X)
     F = int(F.value)
     root_ptr = np.zeros(X.dims[n] + 1, dtype=np.int64)
@@ -378,6 +413,18 @@ def tucker_gram(Y1, Y2=None):
                               Y2.shape[1] if Y2 is not None else 0, rows, _dptr(M), _stream()),
            "tucker_gram")
     return M
+
+
+def tucker_gemm(A, B):
+    """C = A B in FP64 accuracy on the tensor cores (A: m x K, B: K x n)."""
+    torch = _torch()
+    A, B = _dev_f64(A), _dev_f64(B)
+    m, K = A.shape
+    n = B.shape[1]
+    C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    _check(_lib().tucker_gemm(_dptr(A), max(K, 1), _dptr(B), n, m, n, K, _dptr(C), n, _stream()),
+           "tucker_gemm")
+    return C
 
 
 def tucker_gram_noalloc(Y1, Y2=None, M=None):
@@ -529,3 +576,121 @@ def header_functions(header_path=None):
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(tucker_[a-z0-9_]+)\s*\(", text)))
+
+
+# ---- fourth-order tensors ----------------------------------------------------------------------
+
+class Tensor4(Tensor):
+    """Owning wrapper of a tucker4_tensor handle."""
+
+    def close(self):
+        if self.handle:
+            _lib().tucker4_tensor_destroy(self.handle)
+            self.handle = None
+
+
+def tucker4_tensor_create(idx, val, dims) -> Tensor4:
+    """idx: int32 [4, nnz], val: float64 [nnz]; host (numpy / CPU) or CUDA tensors."""
+    torch = _torch()
+    coo = tucker4_coo()
+    for a in range(4):
+        coo.dims[a] = int(dims[a])
+    if isinstance(idx, torch.Tensor) and idx.is_cuda:
+        idx_t = idx.to(torch.int32).contiguous()
+        val_t = val.to(torch.float64).contiguous()
+        keep = [idx_t, val_t]
+        coo.nnz = int(val_t.numel())
+        for a in range(4):
+            coo.idx[a] = idx_t[a].data_ptr() if coo.nnz else None
+        coo.val = val_t.data_ptr() if coo.nnz else None
+        coo.where = TUCKER_DEVICE
+    else:
+        idx_h = np.ascontiguousarray(np.asarray(idx), dtype=np.int32)
+        val_h = np.ascontiguousarray(np.asarray(val), dtype=np.float64)
+        keep = [idx_h, val_h]
+        coo.nnz = int(val_h.shape[0])
+        for a in range(4):
+            coo.idx[a] = idx_h[a].ctypes.data if coo.nnz else None
+        coo.val = val_h.ctypes.data if coo.nnz else None
+        coo.where = TUCKER_HOST
+    h = c_void_p()
+    _check(_lib().tucker4_tensor_create(ctypes.byref(coo), _stream(), ctypes.byref(h)),
+           "tucker4_tensor_create")
+    del keep
+    return Tensor4(h, dims)
+
+
+def tucker4_tensor_info(X: Tensor4):
+    nnz, n2 = c_int64(), c_double()
+    _check(_lib().tucker4_tensor_info(X.handle, ctypes.byref(nnz), ctypes.byref(n2)),
+           "tucker4_tensor_info")
+    return int(nnz.value), float(n2.value)
+
+
+def _run4(fn_name, X: Tensor4, J, tol, max_iter, init, out="device"):
+    torch = _torch()
+    o = tucker4_opts()
+    o.precision = TUCKER_FP64
+    o.tol = float(tol)
+    o.max_iter = int(max_iter)
+    o.init_where = TUCKER_DEVICE
+    o.stream = _stream().value
+    o.flags = 0
+    keep = []
+    if init is not None:
+        for a in range(4):
+            if init[a] is not None:
+                t = _dev_f64(init[a])
+                keep.append(t)
+                o.init[a] = t.data_ptr()
+    if out == "host":
+        alloc = lambda shape: torch.empty(shape, dtype=torch.float64).pin_memory()  # noqa: E731
+        where = TUCKER_HOST
+    else:
+        alloc = lambda shape: torch.empty(shape, dtype=torch.float64, device="cuda")  # noqa: E731
+        where = TUCKER_DEVICE
+    G = alloc(tuple(int(j) for j in J))
+    U = [alloc((X.dims[a], int(J[a]))) for a in range(4)]
+    fh = alloc((max(1, int(max_iter)),))
+    r = tucker4_result()
+    r.G = G.data_ptr()
+    for a in range(4):
+        r.U[a] = U[a].data_ptr()
+    r.fit_history = fh.data_ptr()
+    r.where = where
+    Jc = (c_int32 * 4)(*[int(j) for j in J])
+    _check(getattr(_lib(), fn_name)(X.handle, Jc, ctypes.byref(o), ctypes.byref(r)), fn_name)
+    iters = int(r.iters)
+    return dict(G=G, U=U, fit=float(r.fit), iters=iters,
+                fit_history=fh[:iters].cpu().numpy().tolist(),
+                rank_deficient=int(r.rank_deficient))
+
+
+def tucker4_hosvd(X: Tensor4, J, out="device"):
+    return _run4("tucker4_hosvd", X, J, 0.0, 1, None, out)
+
+
+def tucker4_hooi(X: Tensor4, J, tol=1e-4, max_iter=50, init=None, out="device"):
+    return _run4("tucker4_hooi", X, J, tol, max_iter, init, out)
+
+
+def tucker4_sp(X: Tensor4, J, D_raw, tol=1e-4, max_iter=50, out="device"):
+    return _run4("tucker4_sp", X, J, tol, max_iter, [None, None, None, D_raw], out)
+
+
+def tucker4_mp(X: Tensor4, J, tol=1e-4, max_iter=50, init=None, out="device"):
+    return _run4("tucker4_mp", X, J, tol, max_iter, init, out)
+
+
+def tucker4_ttmc(X: Tensor4, n, U):
+    """Z_(n) of Figure hooin (N = 4) for the factors U (U[n] unused): I_n x prod_{a != n} J_a."""
+    torch = _torch()
+    Ud = [None if a == n else _dev_f64(U[a]) for a in range(4)]
+    J = [1 if a == n else int(Ud[a].shape[1]) for a in range(4)]
+    cols = int(np.prod([J[a] for a in range(4) if a != n]))
+    Y = torch.empty((X.dims[n], cols), dtype=torch.float64, device="cuda")
+    ptrs = (c_void_p * 4)(*[None if a == n else Ud[a].data_ptr() for a in range(4)])
+    Jc = (c_int32 * 4)(*J)
+    _check(_lib().tucker4_ttmc(X.handle, int(n), ctypes.cast(ptrs, c_void_p), Jc, _dptr(Y),
+                               _stream()), "tucker4_ttmc")
+    return Y

@@ -1,12 +1,17 @@
-"""bench.py's host-side arithmetic on CPU: the roofline object (achieved rate per launch, the
-ncu-derived traffic), the TTMc rates, the clock summary and the peak file."""
+"""bench.py's host-side arithmetic on CPU: the roofline object (achieved rate per launch), the
+projection rates, the clock summary, the peak file, and the oracle's step timed in units (the
+unit cycle must reproduce the oracle's own HOOI and MP passes)."""
 import math
 import os
 import sys
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
+from oracle import tucker_oracle as O  # noqa: E402
+from paper_0711_2023_gb300 import synth  # noqa: E402
 
 
 def test_roofline_of():
@@ -15,30 +20,20 @@ def test_roofline_of():
     r = bench.roofline_of(prof, "k", 16.0, "tensor", 2000.0, "TFLOP/s", "test")
     assert math.isclose(r["achieved"], 1000.0) and math.isclose(r["frac"], 0.5)
     assert math.isclose(r["share_of_step"], 0.5) and r["launches"] == 4
-    assert r["traffic"] is None                       # no ncu ratio for this kernel
+    assert r["traffic"] is None
+    assert math.isclose(r["algorithmic_bytes"], 1e9)
     assert bench.roofline_of(prof, "missing", 16.0, "alu", 1.0, "TFLOP/s", "t") is None
-    # GB/s roof from bytes
-    g = bench.roofline_of(prof, "k", 16.0, "hbm", 1000.0, "GB/s", "t", per="bytes")
-    assert math.isclose(g["achieved"], 500.0)         # 1e9 B / 2e-3 s
-
-
-def test_ncu_traffic_ratio():
-    # traffic per launch = (ncu DRAM bytes / algorithmic bytes of the capture) x algorithmic bytes
-    assert 0.8 < bench.NCU_TRAFFIC_RATIO["syrk_f64"] < 1.1
-    assert 1.0 <= bench.NCU_TRAFFIC_RATIO["gram_bf16x3"] < 1.2
-    prof = {"syrk_f64": {"launches": 2, "ms": 2.0, "flops": 2e9, "bytes": 2e8}}
-    r = bench.roofline_of(prof, "syrk_f64", 4.0, "alu", 1.25, "TFLOP/s", "t")
-    assert math.isclose(r["traffic"], bench.NCU_TRAFFIC_RATIO["syrk_f64"] * 1e8)
-    assert math.isclose(r["algorithmic_bytes"], 1e8)
+    t = bench.roofline_of(prof, "k", 16.0, "tensor", 2000.0, "TFLOP/s", "t", traffic=1.5e9)
+    assert t["traffic"] == 1.5e9
 
 
 def test_ttmc_rates():
     prof = {"ttmc_mixed": {"launches": 10, "ms": 5.0, "flops": 5e10, "bytes": 1e9}}
-    r = bench.ttmc_rates(prof, "ttmc_mixed", 80.0, 8000.0)
+    r = bench.ttmc_rates(prof, "ttmc_mixed", 80.0, 8000.0, "n")
     assert math.isclose(r["algorithmic_gbs"], 200.0) and math.isclose(r["frac_hbm"], 0.025)
     assert math.isclose(r["tflops"], 10.0) and math.isclose(r["frac_alu"], 0.125)
     assert math.isclose(r["ms_per_launch"], 0.5)
-    assert bench.ttmc_rates({}, "ttmc_mixed", 80.0, 8000.0) is None
+    assert bench.ttmc_rates({}, "ttmc_mixed", 80.0, 8000.0, "n") is None
 
 
 def test_parse_clocks():
@@ -59,3 +54,31 @@ def test_load_peaks_reads_measured_file():
     peaks, src = bench.load_peaks()
     assert src in ("measured", "fallback")
     assert peaks["hbm_gbs"] > 1000 and peaks["bf16_tflops"] > 100
+
+
+def test_estimate_step_seconds():
+    times = {u: [] for u in bench.REFERENCE_UNITS}
+    for i, u in enumerate(bench.REFERENCE_UNITS):
+        times[u] = [1.0 + i, 3.0 + i]              # mean 2 + i
+    s, missing = bench.estimate_step_seconds(times)
+    assert math.isclose(s, sum(2.0 + i for i in range(10))) and missing == []
+    part = {u: ([2.0] if i < 4 else []) for i, u in enumerate(bench.REFERENCE_UNITS)}
+    s, missing = bench.estimate_step_seconds(part)
+    assert math.isclose(s, 20.0) and len(missing) == 6
+
+
+def test_unit_cycle_reproduces_the_oracle_passes(monkeypatch):
+    # The ten units, run in order, are exactly one HOOI pass and one MP pass from the start.
+    monkeypatch.setattr(bench, "CORE", (4, 3, 5))
+    X = synth.random_sparse_tensor((12, 10, 9), 300, synth.config_seed(77))
+    start = bench.oracle_start(X, None, None)
+    st = bench.OracleStep(X, start)
+    for u in bench.REFERENCE_UNITS:
+        st.run(u)
+    h = O.hooi(X.dims, X.idx, X.val, (4, 3, 5), -np.inf, 1, init=start)
+    m = O.mp(X.dims, X.idx, X.val, (4, 3, 5), -np.inf, 1, init=start)
+    assert abs(st.fits["hooi"] - h["fit"]) <= 1e-14
+    assert abs(st.fits["mp"] - m["fit"]) <= 1e-14
+    # the MP start given explicitly equals the pseudo HO-SVD start (same leading eigenvectors)
+    m0 = O.mp(X.dims, X.idx, X.val, (4, 3, 5), -np.inf, 1)
+    assert abs(m0["fit"] - m["fit"]) <= 1e-12

@@ -30,7 +30,7 @@ def _rank(rank, world, port, out):
     assert (w, r) == (world, rank) and dist.get_backend() == "gloo"
     bench.barrier(w)
     assert bench.max_over_ranks(float(10 * (rank + 1)), w) == 10.0 * world
-    X, C_raw = bench.make_inputs(r)
+    X = bench.make_inputs(r)
     # every rank's tensor is its own: gather a fingerprint of each
     fp = torch.tensor([float(X.val.sum()), float(X.idx[0].astype(np.int64).sum())],
                       dtype=torch.float64)

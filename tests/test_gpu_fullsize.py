@@ -1,5 +1,4 @@
-"""Full-size checks on the benchmark workload (1000^3, 1e7 nonzeros, core 50^3), in the launch
-configuration the benchmark times.  The oracle cannot run every pass at this size, so it checks
+"""Full-size checks on the 1000^3 workload (1e7 nonzeros, core 50^3) for all four methods.  The oracle cannot run every pass at this size, so it checks
 what it can compute directly from the GPU's output: the core and fit of the returned factors
 (which must equal the GPU's own), and that the last factor updated spans the leading
 eigenspace of the matrix the method defines for it (built by the oracle from the other
@@ -63,3 +62,14 @@ def test_hosvd_fullsize(tucker_lib, big):
     g = tucker_lib.tucker_hosvd(T, J)
     U = check_core_fit(X, g)
     check_leading(O.unfolding_gram(X.dims, X.idx, X.val, 0), U[0])
+
+
+def test_sp_fullsize(tucker_lib, big):
+    X, T = big
+    C_raw = synth.uniform_matrix(DIMS[2], J[2], synth.config_seed(2))
+    g = tucker_lib.tucker_sp(T, J, C_raw, tol=-np.inf, max_iter=2)
+    assert g["iters"] == 2
+    U = check_core_fit(X, g)
+    # C, the last factor of a pass, from B: Gram((X x_2 B^T)_(3)) (Figure sp3)
+    Y = O.ttm(X.dims, X.idx, X.val, 1, U[1])
+    check_leading(O.gram(O.unfold_dense(Y, 2)), U[2])

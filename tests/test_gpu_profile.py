@@ -25,8 +25,10 @@ def test_profile_records_and_counters(tucker_lib):
     r = tk.tucker_hooi(T, J, tol=-np.inf, max_iter=2)
     torch.cuda.synchronize()
     assert tk.tucker_launch_count() > n0
-    n, ms, fl, by = tk.tucker_profile_query("syrk_f64")
+    n, ms, fl, by = tk.tucker_profile_query("gram_f64_tc")
     assert n == 6 and ms > 0 and fl > 0 and by > 0   # three modes, two passes
+    n, ms, fl, by = tk.tucker_profile_query("gram_ozaki")
+    assert n == 6 and ms > 0 and fl > 0 and by > 0   # its tensor-core kernel
     n, ms, _, _ = tk.tucker_profile_query("eig_topk")
     assert n == 6 + 2 and ms > 0                      # plus the HO-SVD start of B and C
     n_out, _, outer, _ = tk.tucker_profile_query("eig_outer")
@@ -37,7 +39,7 @@ def test_profile_records_and_counters(tucker_lib):
     tk.tucker_profile_enable(False)
     # nothing recorded once off, and the next calls still run
     r2 = tk.tucker_hooi(T, J, tol=-np.inf, max_iter=2)
-    assert tk.tucker_profile_query("syrk_f64")[0] == 0
+    assert tk.tucker_profile_query("gram_f64_tc")[0] == 0
     assert r2["fit_history"] == r["fit_history"]
     T2 = make(tk, (50, 40, 30), 5_000, 12)
     tk.tucker_hosvd(T2, (5, 5, 5))

@@ -31,6 +31,17 @@ def test_gram_noalloc_matches_gram_twice(tucker_lib):
     assert np.array_equal(M_new, M_new.T)
 
 
+def test_gram_noalloc_largest_size(tucker_lib):
+    # rows = 1448 is the largest the fixed scratch allows: one K split whose partial tiles fill
+    # the array almost to its end
+    Y = synth.uniform_matrix(1448, 4096, 14) - 0.5
+    M_ref = tucker_lib.tucker_gram(Y).cpu().numpy()
+    for _ in range(2):
+        M_new = tucker_lib.tucker_gram_noalloc(Y).cpu().numpy()
+        assert rel_err(M_new, M_ref) <= RTOL
+        assert np.array_equal(M_new, M_new.T)
+
+
 def test_gram_noalloc_rejects_oversize(tucker_lib):
     import torch
     Y = torch.zeros((1449, 64), dtype=torch.float64, device="cuda")
