@@ -15,6 +15,8 @@ of B and C is computed once.  One step = one HOOI pass and one MP pass, each fro
                 cores and factors copied out, all inside the timed region
   batched       256 independent small tensors (dims 30..300, density 1..20 %, cores 4..32),
                 HOOI + MP, 10 passes each, mixed, through the batched entry points
+  streamed      MP with the tensor's orderings in pinned host memory, streamed to the GPU in
+                chunks (the out-of-core form), one pass from the same start
   roofline      the FP64 step's dominant kernel, achieved = algorithmic FLOPs / its event-timed
                 device time; roofline_gram in `mixed` does the same for the tensor-core Gram
   cpu_baseline  the FP64 oracle on this host's cores, on a bounded sample of the same step
@@ -184,7 +186,9 @@ KERNELS = ("gram_f64_tc", "gram_ozaki", "gemm_ozaki", "ozaki_split", "syrk_f64",
            "chol_f64", "jacobi_f64", "csf_build")
 # spans that contain several of the kernels above
 STAGES = ("gram_f64_tc", "eig_topk", "syev_refined", "syev_jacobi32")
-COUNTERS = ("eig_outer", "syev_steps", "syev_fp32_sweeps", "syev_fallback")   # eigensolver iteration counts
+# eigensolver counters: iterations, and per solve its kernel launches and host synchronisations
+COUNTERS = ("eig_outer", "syev_steps", "syev_fp32_sweeps", "syev_fallback", "eig_launches",
+            "eig_host_syncs")
 
 
 def timed_region(tk, torch, world, local, steps, T, start, l2buf, precision, profile=False):
@@ -449,6 +453,30 @@ def batched_run(steps, warmup, count=256, sweeps=10):
                                    "sample": f"first {ns} tensors, HOOI + MP"}}
 
 
+def streamed_run(X, start, budget=2 << 30, passes=1):
+    """MP on the workload's tensor with its orderings in pinned host memory, streamed to the
+    device in chunks of at most `budget` device bytes (the out-of-core form of SP/MP): build
+    time, one pass from the start, and the host-to-device rate achieved while streaming."""
+    import torch
+    from paper_0711_2023_gb300 import tucker as tk
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = tk.tucker_stream_create(X.idx, X.val, X.dims, budget)
+    build_s = time.perf_counter() - t0
+    _, _, chunks = tk.tucker_stream_info(S)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = tk.tucker_mp_streamed(S, CORE, tol=-np.inf, max_iter=passes, init=start)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    S.close()
+    return {"value": passes / dt, "unit": "sweeps/s", "method": "MP", "passes": passes,
+            "device_budget_bytes": budget, "chunks": chunks, "build_s": build_s,
+            "h2d_gbs_while_streaming": r["bytes_streamed"] / dt / 1e9, "fit": r["fit"],
+            "note": "orderings in pinned host memory, chunks copied over NVLink-C2C while the "
+                    "previous chunk's projection and Gram run"}
+
+
 def batched_leg(args):
     from paper_0711_2023_gb300 import build, tucker as tk
     build.build()
@@ -530,6 +558,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="leave the batched workload out of the default line")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-streamed", action="store_true",
+                    help="leave the host-streamed (out-of-core) MP out of the default line")
     ap.add_argument("--profile-leg", choices=["fp64", "mixed"], default=None,
                     help="run only warm-up + timed steps of one precision form (for ncu "
                          "captures) and print a short summary line")
@@ -627,6 +657,10 @@ def main():
     batched = None
     if not args.no_batched:
         batched = batched_run(steps=2, warmup=1)
+    streamed = None
+    if not args.no_streamed:
+        streamed = streamed_run(X, start)
+        streamed["dfit_vs_in_memory"] = abs(streamed["fit"] - fits["mp"])
 
     if rank != 0:
         return
@@ -688,6 +722,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "batched": batched,
+        "streamed": streamed,
         "gpu_launches": launches,
         "clocks": clk,
         "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs"),

@@ -172,6 +172,27 @@ int tucker4_mp(tucker4_tensor X, const int32_t J[4], const tucker4_opts* opts, t
 int tucker4_ttmc(tucker4_tensor X, int32_t n, const double* const d_U[4], const int32_t J[4],
                  double* d_Y, void* stream);
 
+/* ---- tensors streamed from host memory ---------------------------------------------------
+ * Slice Projection and Multislice Projection for tensors whose orderings do not fit in device
+ * memory (the paper's reason for SP and MP: their matrices are sums over slices, so the tensor
+ * can be read one slice after another; Section 3 "Slice Projection").  tucker_stream_create
+ * keeps the slice-major orderings of X in pinned host memory, building them chunk by chunk on
+ * the GPU so that at most `budget` bytes of device memory are used for one chunk (budget >= 64
+ * KiB; duplicates summed, indices checked: EINVAL).  tucker_sp_streamed / tucker_mp_streamed run
+ * the methods with the same arguments and results as tucker_sp / tucker_mp (FP64 form only),
+ * streaming the chunks over NVLink-C2C with copies overlapped with the work on the previous
+ * chunk; *bytes_streamed (may be NULL) receives the host-to-device bytes moved.
+ * tucker_stream_info reports the distinct nonzeros, |X|_F^2 and the number of chunks. */
+typedef struct tucker_stream_s* tucker_stream_tensor;
+int tucker_stream_create(const tucker_coo* X, int64_t budget, void* stream,
+                         tucker_stream_tensor* out);
+int tucker_stream_destroy(tucker_stream_tensor X);
+int tucker_stream_info(tucker_stream_tensor X, int64_t* nnz, double* norm2, int64_t* chunks);
+int tucker_sp_streamed(tucker_stream_tensor X, const int32_t J[3], const tucker_opts* opts,
+                       tucker_result* out, double* bytes_streamed);
+int tucker_mp_streamed(tucker_stream_tensor X, const int32_t J[3], const tucker_opts* opts,
+                       tucker_result* out, double* bytes_streamed);
+
 const char* tucker_strerror(int status);
 /* Text of the last CUDA failure seen by the calling thread (empty if none). */
 const char* tucker_last_error_detail(void);
@@ -259,6 +280,15 @@ int tucker_gram_bf16x3(const uint16_t* d_Y1hi, const uint16_t* d_Y1lo, int64_t K
                        const uint16_t* d_Y2hi, const uint16_t* d_Y2lo, int64_t K2, int64_t ld2,
                        int32_t rows, double* d_M, void* stream);
 
+/* M = sum over one or two terms of Gram((X x_m U_m^T)_(n)) (Figures sp3, mp3) in the mixed form,
+ * fused: the FP32 projection is built in shared memory, split into BF16 hi + lo and fed to the
+ * tensor cores (hi hi^T + hi lo^T + lo hi^T, FP32 accumulation per K range, FP64 sum), so the
+ * projection never goes to memory.  For modes of at most 256 rows (EINVAL above); the methods'
+ * mixed form uses it for such modes.  d_U1 (I_m1 x J1), d_U2 (I_m2 x J2) FP32 row-major; pass
+ * m2 = -1 for one term.  M rows x rows FP64, exactly symmetric. */
+int tucker_gram_fused(tucker_tensor X, int32_t n, int32_t m1, const float* d_U1, int32_t J1,
+                      int32_t m2, const float* d_U2, int32_t J2, double* d_M, void* stream);
+
 /* J leading eigenvectors of the symmetric positive semi-definite n x n matrix M (largest
  * eigenvalue first; in each column the entry of largest magnitude is positive).  d_U0
  * (n x J, may be NULL) is a starting guess.  Outputs d_U (n x J) and d_lambda (J).
@@ -293,7 +323,8 @@ int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const dou
  * refinement steps of one small eigenproblem), "syev_fp32_sweeps" (value: sweeps of its FP32
  * Jacobi), "syev_fallback" (value 1: unresolved cluster,
  * 2: step limit, 3: order above the shared-memory limit), "eig_outer" (value: Rayleigh-Ritz
- * iterations of one solve).  Every name and the argument order are fixed; unknown names
+ * iterations of one solve), "eig_launches" and "eig_host_syncs" (value: the kernel launches and
+ * host synchronisations of one solve).  Every name and the argument order are fixed; unknown names
  * report zero.  tucker_launch_count returns the number of kernels this library has launched
  * in the process. */
 /* ---- autotuning (no counterpart in the paper) -------------------------------------------

@@ -279,7 +279,7 @@ int hooi_matrix(Run& r, int n) {
   TK_TRY(ordering(r, n, m, o, &ord));
   const int64_t K = (int64_t)r.J[m] * r.J[o];
   if (!r.mixed) {
-    TK_TRY(ttmc_f64(r.X, ord, r.U[m].as<double>(), r.J[m], r.U[o].as<double>(), r.J[o],
+    TK_TRY(ttmc_fp64(r.X, ord, r.U[m].as<double>(), r.J[m], r.U[o].as<double>(), r.J[o],
                     r.Y.as<double>(), r.s));
     return gram_f64_tc((int)r.dim(n), r.Y.as<double>(), K, nullptr, 0, r.M.as<double>(), r.s);
   }
@@ -313,8 +313,27 @@ int slice_term(Run& r, int n, int m, int which, GramTerm* t) {
   return TUCKER_OK;
 }
 
-// Mode-n matrix of SP (one term, Figure sp3) or MP (two terms, Figure mp3).
+// Mode-n matrix of SP (one term, Figure sp3) or MP (two terms, Figure mp3).  In the mixed form
+// a mode of at most 256 rows takes the fused kernel (the projection never leaves shared memory).
 int slice_matrix(Run& r, int n, int m1, int m2) {
+  if (r.mixed && r.dim(n) <= FUSED_GRAM_MAX_ROWS) {
+    const int nt = m2 >= 0 ? 2 : 1;
+    const int ms[2] = {m1, m2};
+    const Ordering* ords[2] = {nullptr, nullptr};
+    const float* U[2] = {nullptr, nullptr};
+    int64_t ld[2] = {0, 0};
+    int J[2] = {0, 0};
+    for (int t = 0; t < nt; ++t) {
+      Ordering* ord;
+      TK_TRY(ordering(r, n, 3 - n - ms[t], ms[t], &ord));
+      TK_TRY(ensure_fiber_map(r.X, ord, r.s));
+      ords[t] = ord;
+      U[t] = r.U32[ms[t]].as<float>();
+      ld[t] = factor_ld32(r.J[ms[t]]);
+      J[t] = r.J[ms[t]];
+    }
+    return gram_fused_mixed(r.X, n, nt, ords, U, ld, J, r.M.as<double>(), r.s);
+  }
   GramTerm t[2];
   TK_TRY(slice_term(r, n, m1, 0, &t[0]));
   const int nt = m2 >= 0 ? 2 : 1;
@@ -333,7 +352,7 @@ int core_and_fit(Run& r, bool w_ready, double* fit, double* g2) {
   const int64_t nW = r.dim(2) * r.J[0] * r.J[1];
   if (!r.mixed) {
     if (!w_ready)
-      TK_TRY(ttmc_f64(r.X, ord, r.U[0].as<double>(), r.J[0], r.U[1].as<double>(), r.J[1],
+      TK_TRY(ttmc_fp64(r.X, ord, r.U[0].as<double>(), r.J[0], r.U[1].as<double>(), r.J[1],
                       r.Y.as<double>(), r.s));
   } else {
     if (!w_ready)
@@ -354,7 +373,7 @@ int core_and_fit(Run& r, bool w_ready, double* fit, double* g2) {
   // 1e-5 while the residual |X - X^| is above 1% of |X|; closer to exact recovery the mixed
   // form recomputes the core from the FP64 factors with the FP64 projection.
   if (r.mixed && h[1] > 0.99) {
-    TK_TRY(ttmc_f64(r.X, ord, r.U[0].as<double>(), r.J[0], r.U[1].as<double>(), r.J[1],
+    TK_TRY(ttmc_fp64(r.X, ord, r.U[0].as<double>(), r.J[0], r.U[1].as<double>(), r.J[1],
                     r.Y.as<double>(), r.s));
     TK_TRY(core_from_ttmc3(r.Y.as<double>(), (int)r.dim(2), r.J[0], r.J[1], r.U[2].as<double>(),
                            r.J[2], r.G.as<double>(), r.sc.as<double>(), r.s));
@@ -735,7 +754,7 @@ int tucker_ttmc(tucker_tensor X, int32_t n, const double* d_Um, int32_t Jm, cons
   cudaStream_t s = (cudaStream_t)stream;
   Ordering* ord;
   TK_TRY(ensure_ordering(X, n, m, o, s, &ord));
-  TK_TRY(ttmc_f64(X, ord, d_Um, Jm, d_Uo, Jo, d_Y, s));
+  TK_TRY(ttmc_fp64(X, ord, d_Um, Jm, d_Uo, Jo, d_Y, s));
   TK_CUDA(cudaStreamSynchronize(s));
   return TUCKER_OK;
 }
@@ -758,6 +777,31 @@ int tucker_gram(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2, 
   if ((!d_Y1 && K1 != 0) || !d_M || rows < 1 || K1 < 0 || (d_Y2 && K2 < 0)) return TUCKER_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   TK_TRY(gram_f64_tc(rows, d_Y1, K1, d_Y2, d_Y2 ? K2 : 0, d_M, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+
+int tucker_gram_fused(tucker_tensor X, int32_t n, int32_t m1, const float* d_U1, int32_t J1,
+                      int32_t m2, const float* d_U2, int32_t J2, double* d_M, void* stream) {
+  if (!X || n < 0 || n > 2 || m1 < 0 || m1 > 2 || m1 == n || !d_U1 || J1 < 1 || !d_M)
+    return TUCKER_EINVAL;
+  const int nt = m2 >= 0 ? 2 : 1;
+  if (nt == 2 && (m2 > 2 || m2 == n || m2 == m1 || !d_U2 || J2 < 1)) return TUCKER_EINVAL;
+  if (X->dims[n] > FUSED_GRAM_MAX_ROWS) return TUCKER_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ms[2] = {m1, m2};
+  const Ordering* ords[2] = {nullptr, nullptr};
+  for (int t = 0; t < nt; ++t) {
+    Ordering* ord;
+    TK_TRY(ensure_ordering(X, n, 3 - n - ms[t], ms[t], s, &ord));
+    TK_TRY(ensure_val_f32(X, ord, s));
+    TK_TRY(ensure_fiber_map(X, ord, s));
+    ords[t] = ord;
+  }
+  const float* U[2] = {d_U1, d_U2};
+  const int64_t ld[2] = {J1, J2};
+  const int J[2] = {J1, J2};
+  TK_TRY(gram_fused_mixed(X, n, nt, ords, U, ld, J, d_M, s));
   TK_CUDA(cudaStreamSynchronize(s));
   return TUCKER_OK;
 }
@@ -856,7 +900,7 @@ int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const dou
   Buf Y, g2;
   TK_TRY(Y.alloc(sizeof(double) * X->dims[2] * J[0] * J[1], s));
   TK_TRY(g2.alloc(sizeof(double), s));
-  TK_TRY(ttmc_f64(X, ord, d_A, J[0], d_B, J[1], Y.as<double>(), s));
+  TK_TRY(ttmc_fp64(X, ord, d_A, J[0], d_B, J[1], Y.as<double>(), s));
   TK_TRY(core_from_ttmc3(Y.as<double>(), (int)X->dims[2], J[0], J[1], d_C, J[2], d_G,
                          g2.as<double>(), s));
   double h = 0.0;

@@ -38,6 +38,10 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 void set_error_detail(const char* msg);
 void keep_pool_memory();  // once per device: freed work buffers stay in the stream pool
 void count_launch();
+// Stream synchronisation that the host waits on (counted per host thread), and the counters.
+int host_sync(cudaStream_t s);
+long long host_sync_count();
+long long launch_count();
 // While profiling is enabled, records one occurrence of the counter `name` with `value`
 // (tucker_profile_query reports the occurrences as launches and the sum of values as flops).
 void prof_count(const char* name, double value);

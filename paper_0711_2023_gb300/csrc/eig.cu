@@ -694,7 +694,7 @@ int jacobi_eig(const double* A, int mreal, int64_t lda, double* Qout, double* ev
   TK_LAUNCH();
   int hctl[4];
   TK_CUDA(cudaMemcpyAsync(hctl, ctl.p, sizeof(hctl), cudaMemcpyDeviceToHost, s));
-  TK_CUDA(cudaStreamSynchronize(s));
+  TK_TRY(host_sync(s));
   if (sweeps) *sweeps = hctl[3];
   if (hctl[2] & DEV_TIMEOUT) return TUCKER_ETIMEOUT;
   if (hctl[2] & DEV_NOT_CONVERGED) return TUCKER_ENOTCONV;
@@ -812,13 +812,13 @@ int cholqr_pass_inverse(EigOps& e, double* V, int64_t ldv, int n, int k, const C
     TK_LAUNCH();
     int h = 0;
     TK_CUDA(cudaMemcpyAsync(&h, stat, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TK_CUDA(cudaStreamSynchronize(s));
+    TK_TRY(host_sync(s));
     if (!(h & DEV_CHOL_BREAKDOWN)) break;
     if (attempt == 1) return TUCKER_EINTERNAL;
     std::vector<double> diag(k);
     TK_CUDA(cudaMemcpy2DAsync(diag.data(), sizeof(double), w.Gk, sizeof(double) * (k + 1),
                               sizeof(double), k, cudaMemcpyDeviceToHost, s));
-    TK_CUDA(cudaStreamSynchronize(s));
+    TK_TRY(host_sync(s));
     double tr = 0.0;
     for (double d : diag) tr += d;
     shift = 11.0 * ((double)n * k + (double)k * (k + 1)) * 2.220446049250313e-16 * tr;
@@ -869,7 +869,7 @@ int cholqr2(EigOps& e, double* V, int64_t ldv, int n, int k, const CholWork& w, 
     if (want <= issued) break;
     for (; issued < want; ++issued) TK_TRY(cholqr_pass(e, V, ldv, n, k, w, w.stat + issued, s));
     TK_CUDA(cudaMemcpyAsync(hs, w.stat, sizeof(int) * issued, cudaMemcpyDeviceToHost, s));
-    TK_CUDA(cudaStreamSynchronize(s));
+    TK_TRY(host_sync(s));
     for (; checked < issued; ++checked) {
       if (hs[checked] & DEV_CHOL_BREAKDOWN) return TUCKER_EINTERNAL;
       if (!(hs[checked] & DEV_CHOL_SHIFTED)) ++clean;
@@ -889,8 +889,20 @@ int deflate(EigOps& e, const double* L, int64_t ldl, double* Va, int64_t ldv, in
 
 }  // namespace
 
+namespace {
+// Records the launches and host synchronisations of one solve as profile counters.
+struct EigCounters {
+  long long l0 = launch_count(), s0 = host_sync_count();
+  ~EigCounters() {
+    prof_count("eig_launches", (double)(launch_count() - l0));
+    prof_count("eig_host_syncs", (double)(host_sync_count() - s0));
+  }
+};
+}  // namespace
+
 int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, double* lambda,
                  cudaStream_t s, EigStats* st, const float* M32, double tol) {
+  EigCounters counters;
   ProfScope prof("eig_topk", s, 0.0, 0.0);
   EigStats local;
   if (!st) st = &local;
@@ -914,7 +926,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     std::vector<double> hev(n);
     TK_CUDA(cudaMemcpyAsync(hev.data(), ev.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     if (lambda) TK_CUDA(cudaMemcpyAsync(lambda, ev.p, sizeof(double) * J, cudaMemcpyDeviceToDevice, s));
-    TK_CUDA(cudaStreamSynchronize(s));
+    TK_TRY(host_sync(s));
     st->rank_deficient = !(hev[J - 1] > 1e-13 * std::max(hev[0], 1e-300));
     return TUCKER_OK;
   }
@@ -1027,7 +1039,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     TK_CUDA(cudaMemcpyAsync(thrr.data(), evh, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
     int ozs = 0;
     TK_CUDA(cudaMemcpyAsync(&ozs, ozst.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TK_CUDA(cudaStreamSynchronize(s));
+    TK_TRY(host_sync(s));
     if (ozs & DEV_TIMEOUT) {
       set_error_detail("eigensolver: a bounded wait in a tensor-core product gave up");
       return TUCKER_ETIMEOUT;
@@ -1129,7 +1141,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   if (lambda)
     TK_CUDA(cudaMemcpyAsync(lambda, locked_theta.data(), sizeof(double) * J,
                             cudaMemcpyHostToDevice, s));
-  TK_CUDA(cudaStreamSynchronize(s));
+  TK_TRY(host_sync(s));
   st->rank_deficient = !(locked_theta[J - 1] > 1e-13 * std::max(theta1, 1e-300));
   return TUCKER_OK;
 }

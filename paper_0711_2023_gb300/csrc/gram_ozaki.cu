@@ -71,6 +71,9 @@ __device__ __forceinline__ bool restarts(int d, int j) {
 struct Grid {
   int ntj, npairs, nsplit, nst;
   int sym;
+  // Batched products (one product per slice, each over its own stage range): CTA b computes
+  // tile pair b % npairs of slice b / npairs over stages [stage_start[i], stage_start[i + 1]).
+  const int* stage_start;
 };
 
 struct Job {
@@ -97,6 +100,14 @@ __host__ __device__ inline int pair_index(const Grid& g, int ti, int tj) {
 
 __device__ inline Job job_of(const Grid& g, int b) {
   Job j;
+  if (g.stage_start) {
+    const int i = b / g.npairs, p = b % g.npairs;
+    j.ti = p / g.ntj;
+    j.tj = p % g.ntj;
+    j.s0 = g.stage_start[i];
+    j.ns = g.stage_start[i + 1] - j.s0;
+    return j;
+  }
   const int z = b / g.npairs, p = b % g.npairs;
   pair_tiles(g, p, &j.ti, &j.tj);
   j.s0 = (int)((int64_t)g.nst * z / g.nsplit);
@@ -575,7 +586,7 @@ int oz_gemm_nt(const OzSlices& A, const OzSlices& B, bool sym, double alpha, dou
   const int m = A.rows, n = B.rows;
   const int nti = ceil_div(m, TM), ntj = ceil_div(n, TN);
   const int nst = (int)(A.ldK / KS);
-  Grid g{ntj, 0, 1, nst, sym ? 1 : 0};
+  Grid g{ntj, 0, 1, nst, sym ? 1 : 0, nullptr};
   g.npairs = sym ? nti * (nti + 1) - (ntj < 2 * nti ? 1 : 0) : nti * ntj;
   // K splits: the fewest that fill the SMs' waves to 90 %, each at least 8 stages long.
   const int sms = num_sms();
@@ -651,6 +662,180 @@ int gram_f64_tc(int rows, const double* Y1, int64_t K1, const double* Y2, int64_
   TK_CUDA(cudaStreamSynchronize(s));
   if (h & DEV_TIMEOUT) {
     set_error_detail("FP64 tensor-core Gram: a bounded wait on an mbarrier gave up");
+    return TUCKER_ETIMEOUT;
+  }
+  return TUCKER_OK;
+}
+
+namespace {
+
+// Slices of a gathered, transposed operand for the batched HOOI projection: the K position of
+// fiber f is pos(f) = f + pad[slice of f] (every slice's fibers start on a stage boundary);
+// out[s][j][pos(f)] = digit s of S[src(f)][j] scaled by 2^-ex[j] (src(f) = rows[f], or f when
+// rows is NULL), for j < J.  Positions not written stay zero (the buffer is cleared first).
+// Tiles of 32 fibers x 32 columns through shared memory keep reads and writes coalesced.
+template <int S>
+__global__ void oz_split_gather_kernel(const double* __restrict__ Src, int64_t ld, int J,
+                                       const int32_t* __restrict__ rows, int64_t F,
+                                       const int32_t* __restrict__ fiber_root,
+                                       const int64_t* __restrict__ pad, const int* __restrict__ ex,
+                                       int rows_pad, int64_t ldK, __nv_bfloat16* __restrict__ Q) {
+  __shared__ double tile[32][33];
+  __shared__ int64_t pos_s[32];
+  const int64_t f0 = (int64_t)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;
+  if (threadIdx.y == 0) {
+    const int64_t f = f0 + threadIdx.x;
+    pos_s[threadIdx.x] = f < F ? f + pad[fiber_root[f]] : -1;
+  }
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t f = f0 + i;
+    const int j = j0 + threadIdx.x;
+    double v = 0.0;
+    if (f < F && j < J) v = Src[(rows ? (int64_t)rows[f] : f) * ld + j];
+    tile[i][threadIdx.x] = v;
+  }
+  __syncthreads();
+  const int64_t plane = (int64_t)rows_pad * ldK;
+  const int64_t pos = pos_s[threadIdx.x];
+  if (pos < 0) return;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int j = j0 + i;
+    if (j >= J) continue;
+    oz_cut<S>(oz_fixed<S>(tile[threadIdx.x][i], ex[j]), Q + (int64_t)j * ldK + pos, plane);
+  }
+}
+
+// Y[i, p J_o + q] = 2^(ex_a[p] + ex_b[q] - 14) (hi 2^-21 + lo 2^-7(S-1)) of slice i's product.
+__global__ void oz_reduce_batched(const long long* __restrict__ partial, int ntj, int npairs,
+                                  int nslice, int64_t nslices, int Jm, int Jo,
+                                  const int* __restrict__ exA, const int* __restrict__ exB,
+                                  double* __restrict__ Y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)Jm * Jo;
+  if (t >= nslices * per) return;
+  const int64_t i = t / per;
+  const int p = (int)((t % per) / Jo), q = (int)(t % Jo);
+  const int ti = p / TM, tj = q / TN;
+  const long long* P = partial + (i * npairs + (int64_t)ti * ntj + tj) * 2 * TM * TN;
+  const int rr = p - ti * TM, cc = q - tj * TN;
+  const long long hi = P[rr * TN + cc], lo = P[TM * TN + rr * TN + cc];
+  const int E = exA[p] + exB[q] - 2 * BETA;
+  Y[t] = ldexp((double)hi, E - 3 * BETA) + ldexp((double)lo, E - (nslice - 1) * BETA);
+}
+
+// Padded K layout of a TTMc ordering: pad[i] = (stage start of slice i) * 32 - root_ptr[i],
+// stage_start[i + 1] = stage_start[i] + ceil(F_i / 32).
+__global__ void slice_stages(const int64_t* __restrict__ root_ptr, int64_t In,
+                             int* __restrict__ nstage) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < In) nstage[i] = (int)((root_ptr[i + 1] - root_ptr[i] + KS - 1) / KS);
+}
+__global__ void slice_pads(const int64_t* __restrict__ root_ptr, const int* __restrict__ stage_start,
+                           int64_t In, int64_t* __restrict__ pad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < In) pad[i] = (int64_t)stage_start[i] * KS - root_ptr[i];
+}
+
+template <int S>
+int split_gather(const double* Src, int64_t ld, int J, const int32_t* rows, int64_t F,
+                 const int32_t* fiber_root, const int64_t* pad, const int* ex, int rows_pad,
+                 int64_t ldK, __nv_bfloat16* Q, cudaStream_t s) {
+  dim3 grid((unsigned)ceil_div(F, 32), (unsigned)ceil_div(J, 32));
+  oz_split_gather_kernel<S><<<grid, dim3(32, 8), 0, s>>>(Src, ld, J, rows, F, fiber_root, pad, ex,
+                                                         rows_pad, ldK, Q);
+  TK_LAUNCH();
+  return TUCKER_OK;
+}
+
+}  // namespace
+
+int ttmc_f64_tc(const tucker_tensor_s* X, const Ordering* o, const double* Um, int Jm,
+                const double* Uo, int Jo, double* Y, cudaStream_t s) {
+  const int64_t In = X->dims[o->n], F = o->F;
+  const int S = OZ_GRAM_SLICES;
+  if (In == 0) return TUCKER_OK;
+  ProfScope prof("ttmc_f64_tc", s, 2.0 * ((double)X->nnz * Jo + (double)F * Jm * Jo),
+                 12.0 * X->nnz + 16.0 * F + 8.0 * In * (double)Jm * Jo);
+  // stage 1 on the CUDA cores: T[f, q] = sum over fiber f's leaves of x U_o[i_o, q]
+  Buf T, nst, sst, pad, exA, exB, tot, part, st;
+  TK_TRY(T.alloc(sizeof(double) * (size_t)std::max<int64_t>(F, 1) * Jo, s));
+  TK_TRY(slice_proj_f64_fibers(F, nullptr, nullptr, o->fiber_ptr, o->leaf_idx, o->val, Uo, Jo, 0,
+                               T.as<double>(), s));
+  // padded stage layout: slice i's fibers start at stage sst[i]
+  TK_TRY(nst.alloc(sizeof(int) * (In + 1), s));
+  TK_TRY(sst.alloc(sizeof(int) * (In + 1), s));
+  TK_TRY(pad.alloc(sizeof(int64_t) * In, s));
+  TK_TRY(tot.alloc(sizeof(unsigned), s));
+  slice_stages<<<ceil_div(In, 256), 256, 0, s>>>(o->root_ptr, In, nst.as<int>());
+  TK_LAUNCH();
+  TK_TRY(exclusive_scan_u32(nst.as<unsigned>(), sst.as<unsigned>(), In, tot.as<unsigned>(), s));
+  unsigned stages = 0;
+  TK_CUDA(cudaMemcpyAsync(&stages, tot.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaMemcpyAsync(sst.as<unsigned>() + In, tot.p, sizeof(unsigned),
+                          cudaMemcpyDeviceToDevice, s));
+  slice_pads<<<ceil_div(In, 256), 256, 0, s>>>(o->root_ptr, sst.as<int>(), In, pad.as<int64_t>());
+  TK_LAUNCH();
+  TK_CUDA(cudaStreamSynchronize(s));
+  const int64_t ldK = std::max<int64_t>((int64_t)stages * KS, KS);
+  // operands: A^T rows p (the fibers' U_m rows), B^T rows q (T); per-column scale exponents
+  OzSlices A, B;
+  A.nslice = B.nslice = S;
+  A.rows = Jm;
+  A.rows_pad = ceil_div(Jm, TM) * TM;
+  B.rows = Jo;
+  B.rows_pad = ceil_div(Jo, TM) * TM;
+  A.ldK = B.ldK = ldK;
+  TK_TRY(A.Q.alloc(sizeof(__nv_bfloat16) * S * (size_t)A.rows_pad * ldK, s));
+  TK_TRY(B.Q.alloc(sizeof(__nv_bfloat16) * S * (size_t)B.rows_pad * ldK, s));
+  TK_TRY(A.ex.alloc(sizeof(int) * A.rows_pad, s));
+  TK_TRY(B.ex.alloc(sizeof(int) * B.rows_pad, s));
+  TK_CUDA(cudaMemsetAsync(A.Q.p, 0, A.Q.bytes, s));
+  TK_CUDA(cudaMemsetAsync(B.Q.p, 0, B.Q.bytes, s));
+  TK_CUDA(cudaMemsetAsync(A.ex.p, 0x80, sizeof(int) * Jm, s));
+  TK_CUDA(cudaMemsetAsync(B.ex.p, 0x80, sizeof(int) * Jo, s));
+  const int64_t Im = X->dims[o->m];
+  oz_scale_cols<<<dim3(ceil_div(Jm, 32), ceil_div(Im, 256)), dim3(32, 8), 0, s>>>(
+      Um, Jm, Im, Jm, A.ex.as<int>());
+  TK_LAUNCH();
+  if (F > 0) {
+    oz_scale_cols<<<dim3(ceil_div(Jo, 32), ceil_div(F, 256)), dim3(32, 8), 0, s>>>(
+        T.as<double>(), Jo, F, Jo, B.ex.as<int>());
+    TK_LAUNCH();
+  }
+  oz_fix_zero_cols<<<ceil_div(Jm, 256), 256, 0, s>>>(Jm, A.ex.as<int>());
+  TK_LAUNCH();
+  oz_fix_zero_cols<<<ceil_div(Jo, 256), 256, 0, s>>>(Jo, B.ex.as<int>());
+  TK_LAUNCH();
+  if (F > 0) {
+    TK_TRY(split_gather<S>(Um, Jm, Jm, o->fiber_idx, F, o->fiber_root, pad.as<int64_t>(),
+                           A.ex.as<int>(), A.rows_pad, ldK, A.Q.as<__nv_bfloat16>(), s));
+    TK_TRY(split_gather<S>(T.as<double>(), Jo, Jo, nullptr, F, o->fiber_root, pad.as<int64_t>(),
+                           B.ex.as<int>(), B.rows_pad, ldK, B.Q.as<__nv_bfloat16>(), s));
+  }
+  // one product per slice: (J_m x J_o) = A_i^T B_i over the slice's stages
+  const int nti = ceil_div(Jm, TM), ntj = ceil_div(Jo, TN);
+  Grid g{ntj, nti * ntj, 1, (int)stages, 0, sst.as<int>()};
+  const int64_t njobs = In * g.npairs;
+  TK_TRY(part.alloc(sizeof(long long) * 2 * TM * TN * (size_t)njobs, s));
+  TK_TRY(st.alloc(sizeof(int), s));
+  TK_CUDA(cudaMemsetAsync(st.p, 0, sizeof(int), s));
+  CUtensorMap mapA, mapB;
+  TK_TRY(make_slice_map(&mapA, A, TM));
+  TK_TRY(make_slice_map(&mapB, B, TN));
+  {
+    ProfScope pk("gemm_ozaki", s, 2.0 * 28.0 * TM * TN * (double)KS * stages * g.npairs,
+                 2.0 * S * ((double)A.rows_pad + B.rows_pad) * ldK + 16.0 * TM * TN * (double)njobs);
+    TK_TRY(launch_products<7>(mapA, mapB, g, njobs, part.as<long long>(), st.as<int>(), s));
+  }
+  oz_reduce_batched<<<ceil_div(In * Jm * Jo, 256), 256, 0, s>>>(
+      part.as<long long>(), ntj, g.npairs, S, In, Jm, Jo, A.ex.as<int>(), B.ex.as<int>(), Y);
+  TK_LAUNCH();
+  int h = 0;
+  TK_CUDA(cudaMemcpyAsync(&h, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  if (h & DEV_TIMEOUT) {
+    set_error_detail("FP64 tensor-core projection: a bounded wait on an mbarrier gave up");
     return TUCKER_ETIMEOUT;
   }
   return TUCKER_OK;

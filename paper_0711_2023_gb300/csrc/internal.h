@@ -59,8 +59,24 @@ int ttmc_f64(const tucker_tensor_s* X, const Ordering* ord, const double* Um, in
              const double* Uo, int Jo, double* Y, cudaStream_t s);
 int slice_proj_f64(const tucker_tensor_s* X, const Ordering* ord, const double* Um, int Jm,
                    double* Y, cudaStream_t s);
+// The same HOOI projection with the fibers' rank updates as per-slice FP64-accurate products on
+// the tensor cores (gram_ozaki.cu), and the dispatcher between the two.
+int ttmc_f64_tc(const tucker_tensor_s* X, const Ordering* ord, const double* Um, int Jm,
+                const double* Uo, int Jo, double* Y, cudaStream_t s);
+int ttmc_fp64(const tucker_tensor_s* X, const Ordering* ord, const double* Um, int Jm,
+              const double* Uo, int Jo, double* Y, cudaStream_t s);
 int unfolding_gram_f64(const tucker_tensor_s* X, const Ordering* rows, const Ordering* fibers,
                        double* M, cudaStream_t s);
+
+// The slice projection and the HOOI projection on an explicit fiber list (a chunk of an
+// ordering): Y[row[f] * ncol * Jm + col[f] * Jm + p] = sum over fiber f's leaves of x U_m[leaf, p];
+// and Y[i] (i < nroots, Jm x Jo) from roots -> fibers (U_m rows) -> leaves (U_o rows).
+int slice_proj_f64_fibers(int64_t F, const int32_t* row, const int32_t* col,
+                          const int64_t* fiber_ptr, const int32_t* leaf_idx, const double* val,
+                          const double* Um, int Jm, int64_t ncol, double* Y, cudaStream_t s);
+int ttmc_f64_roots(int64_t nroots, const int64_t* root_ptr, const int32_t* fiber_idx,
+                   const int64_t* fiber_ptr, const int32_t* leaf_idx, const double* val,
+                   const double* Um, int Jm, const double* Uo, int Jo, double* Y, cudaStream_t s);
 
 // dense.cu (FP64)
 // C[m x n] = alpha * A[m x k] B[k x n] + beta * Xm + gamma * Zm (Xm, Zm optional, same shape
@@ -126,6 +142,14 @@ int oz_gemm_nt(const OzSlices& A, const OzSlices& B, bool sym, double alpha, dou
 // M = Y1 Y1^T (+ Y2 Y2^T), FP64-accurate; same arguments and result as syrk_f64.
 int gram_f64_tc(int rows, const double* Y1, int64_t K1, const double* Y2, int64_t K2, double* M,
                 cudaStream_t s);
+
+// gram_fused.cu: M = sum over 1 or 2 terms of Gram((X x_m U_m^T)_(n)) in the mixed form, the
+// projection built in shared memory and fed to the tensor cores (BF16x3), for I_n <= 256.
+// ord[t] is ordering (n, o, m_t) with its FP32 values and fiber map; Um[t] FP32 (row stride ldm).
+constexpr int FUSED_GRAM_MAX_ROWS = 256;
+int gram_fused_mixed(const tucker_tensor_s* X, int n, int nterms, const Ordering* const ord[2],
+                     const float* const Um[2], const int64_t ldm[2], const int Jm[2], double* M,
+                     cudaStream_t s);
 
 // gram_tc.cu: M = sum_t Y_t Y_t^T on tcgen05 with Y_t = hi + lo (BF16x3), FP64 result.
 struct GramTerm {

@@ -35,6 +35,17 @@ void clear_locked() {
 
 void count_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+thread_local long long t_syncs = 0;
+}
+int host_sync(cudaStream_t s) {
+  ++t_syncs;
+  TK_CUDA(cudaStreamSynchronize(s));
+  return TUCKER_OK;
+}
+long long host_sync_count() { return t_syncs; }
+long long launch_count() { return g_launch_count.load(std::memory_order_relaxed); }
+
 ProfScope::ProfScope(const char* name, cudaStream_t s, double flops, double bytes)
     : name_(name), s_(s), flops_(flops), bytes_(bytes) {
   if (!g_on) return;

@@ -109,7 +109,9 @@ slice_proj_f64_kernel(int64_t F, const int32_t* __restrict__ fiber_root,
   for (int64_t f = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); f < F;
        f += (int64_t)gridDim.x * wpb) {
     const int64_t l0 = fiber_ptr[f], l1 = fiber_ptr[f + 1];
-    double* out = Y + (int64_t)fiber_root[f] * Io * Jm + (int64_t)fiber_idx[f] * Jm;
+    // without a (row, column) map, fiber f's sums form row f of Y (F x Jm)
+    double* out = fiber_root ? Y + (int64_t)fiber_root[f] * Io * Jm + (int64_t)fiber_idx[f] * Jm
+                             : Y + f * Jm;
     for (int pc = 0; pc < Jm; pc += 32 * NP) {
       double acc[NP];
 #pragma unroll
@@ -294,6 +296,14 @@ int ttmc_f64_roots(int64_t nroots, const int64_t* root_ptr, const int32_t* fiber
   (void)grid;
   TK_LAUNCH();
   return TUCKER_OK;
+}
+
+int ttmc_fp64(const tucker_tensor_s* X, const Ordering* o, const double* Um, int Jm,
+              const double* Uo, int Jo, double* Y, cudaStream_t s) {
+  // The rank-J_m J_o updates of the fibers dominate; with enough of them they run as per-slice
+  // products on the tensor cores (FP64-accurate), else on the CUDA cores.
+  if ((int64_t)Jm * Jo >= 2048 && o->F >= 4096) return ttmc_f64_tc(X, o, Um, Jm, Uo, Jo, Y, s);
+  return ttmc_f64(X, o, Um, Jm, Uo, Jo, Y, s);
 }
 
 }  // namespace tk

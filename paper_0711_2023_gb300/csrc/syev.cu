@@ -357,7 +357,7 @@ int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* eval
     TK_LAUNCH();
     if (step >= first_check) {
       TK_CUDA(cudaMemcpyAsync(hs.data(), misc.p, misc.bytes, cudaMemcpyDeviceToHost, s));
-      TK_CUDA(cudaStreamSynchronize(s));
+      TK_TRY(host_sync(s));
       memcpy(hinfo, hs.data() + 4 * m, sizeof(hinfo));
       double hl_max = 0.0;
       for (int j = 0; j < m; ++j) hl_max = std::max(hl_max, fabs(hs[3 * m + j]));

@@ -94,6 +94,15 @@ _SIGS = {
                              POINTER(tucker4_result)]),
     "tucker4_ttmc": (c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_int32), c_void_p,
                                c_void_p]),
+    "tucker_stream_create": (c_int32, [POINTER(tucker_coo), c_int64, c_void_p,
+                                       POINTER(c_void_p)]),
+    "tucker_stream_destroy": (c_int32, [c_void_p]),
+    "tucker_stream_info": (c_int32, [c_void_p, POINTER(c_int64), POINTER(c_double),
+                                     POINTER(c_int64)]),
+    "tucker_sp_streamed": (c_int32, [c_void_p, POINTER(c_int32), POINTER(tucker_opts),
+                                     POINTER(tucker_result), POINTER(c_double)]),
+    "tucker_mp_streamed": (c_int32, [c_void_p, POINTER(c_int32), POINTER(tucker_opts),
+                                     POINTER(tucker_result), POINTER(c_double)]),
     "tucker_strerror": (c_char_p, [c_int32]),
     "tucker_last_error_detail": (c_char_p, []),
     "tucker_ordering": (c_int32, [c_void_p, c_int32, c_int32, c_int32, POINTER(c_int64), c_void_p,
@@ -114,6 +123,8 @@ _SIGS = {
                                           c_void_p, c_void_p, c_int64, c_void_p]),
     "tucker_gram_bf16x3": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_void_p,
                                      c_int64, c_int64, c_int32, c_void_p, c_void_p]),
+    "tucker_gram_fused": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_int32, c_int32,
+                                    c_void_p, c_int32, c_void_p, c_void_p]),
     "tucker_gemm": (c_int32, [c_void_p, c_int64, c_void_p, c_int64, c_int32, c_int32, c_int64,
                               c_void_p, c_int64, c_void_p]),
     "tucker_gram_noalloc": (c_int32, [c_void_p, c_int64, c_void_p, c_int64, c_int32, c_void_p,
@@ -415,6 +426,20 @@ def tucker_gram(Y1, Y2=None):
     return M
 
 
+def tucker_gram_fused(X: Tensor, n, m1, U1, m2=None, U2=None):
+    """Mixed-form M = Gram((X x_m1 U1^T)_(n)) (+ the term of m2, U2), fused (I_n <= 256)."""
+    torch = _torch()
+    U1 = _dev_f32(U1)
+    U2 = _dev_f32(U2) if U2 is not None else None
+    M = torch.empty((X.dims[n], X.dims[n]), dtype=torch.float64, device="cuda")
+    _check(_lib().tucker_gram_fused(X.handle, int(n), int(m1), _dptr(U1), U1.shape[1],
+                                    -1 if m2 is None else int(m2),
+                                    _dptr(U2) if U2 is not None else None,
+                                    U2.shape[1] if U2 is not None else 0, _dptr(M), _stream()),
+           "tucker_gram_fused")
+    return M
+
+
 def tucker_gemm(A, B):
     """C = A B in FP64 accuracy on the tensor cores (A: m x K, B: K x n)."""
     torch = _torch()
@@ -694,3 +719,87 @@ def tucker4_ttmc(X: Tensor4, n, U):
     _check(_lib().tucker4_ttmc(X.handle, int(n), ctypes.cast(ptrs, c_void_p), Jc, _dptr(Y),
                                _stream()), "tucker4_ttmc")
     return Y
+
+
+# ---- tensors streamed from host memory -----------------------------------------------------------
+
+class StreamTensor(Tensor):
+    """Owning wrapper of a tucker_stream_tensor handle (orderings in pinned host memory)."""
+
+    def close(self):
+        if self.handle:
+            _lib().tucker_stream_destroy(self.handle)
+            self.handle = None
+
+
+def tucker_stream_create(idx, val, dims, budget) -> StreamTensor:
+    """idx int32 [3, nnz], val float64 [nnz] (host or CUDA); budget: device bytes per chunk."""
+    torch = _torch()
+    coo = tucker_coo()
+    for a in range(3):
+        coo.dims[a] = int(dims[a])
+    if isinstance(idx, torch.Tensor) and idx.is_cuda:
+        idx_t = idx.to(torch.int32).contiguous()
+        val_t = val.to(torch.float64).contiguous()
+        keep = [idx_t, val_t]
+        coo.nnz = int(val_t.numel())
+        for a in range(3):
+            coo.idx[a] = idx_t[a].data_ptr() if coo.nnz else None
+        coo.val = val_t.data_ptr() if coo.nnz else None
+        coo.where = TUCKER_DEVICE
+    else:
+        idx_h = np.ascontiguousarray(np.asarray(idx), dtype=np.int32)
+        val_h = np.ascontiguousarray(np.asarray(val), dtype=np.float64)
+        keep = [idx_h, val_h]
+        coo.nnz = int(val_h.shape[0])
+        for a in range(3):
+            coo.idx[a] = idx_h[a].ctypes.data if coo.nnz else None
+        coo.val = val_h.ctypes.data if coo.nnz else None
+        coo.where = TUCKER_HOST
+    h = c_void_p()
+    _check(_lib().tucker_stream_create(ctypes.byref(coo), int(budget), _stream(), ctypes.byref(h)),
+           "tucker_stream_create")
+    del keep
+    return StreamTensor(h, dims)
+
+
+def tucker_stream_info(X: StreamTensor):
+    nnz, n2, ch = c_int64(), c_double(), c_int64()
+    _check(_lib().tucker_stream_info(X.handle, ctypes.byref(nnz), ctypes.byref(n2),
+                                     ctypes.byref(ch)), "tucker_stream_info")
+    return int(nnz.value), float(n2.value), int(ch.value)
+
+
+def _run_streamed(fn_name, X, J, tol, max_iter, init, out="device"):
+    torch = _torch()
+    o, keep = _opts("fp64", tol, max_iter, init)
+    if out == "host":
+        alloc = lambda shape: torch.empty(shape, dtype=torch.float64).pin_memory()  # noqa: E731
+        where = TUCKER_HOST
+    else:
+        alloc = lambda shape: torch.empty(shape, dtype=torch.float64, device="cuda")  # noqa: E731
+        where = TUCKER_DEVICE
+    G = alloc(tuple(int(j) for j in J))
+    U = [alloc((X.dims[a], int(J[a]))) for a in range(3)]
+    fh = alloc((max(1, int(max_iter)),))
+    r = tucker_result()
+    r.G = G.data_ptr()
+    for a in range(3):
+        r.U[a] = U[a].data_ptr()
+    r.fit_history = fh.data_ptr()
+    r.where = where
+    moved = c_double()
+    _check(getattr(_lib(), fn_name)(X.handle, _J(J), ctypes.byref(o), ctypes.byref(r),
+                                    ctypes.byref(moved)), fn_name)
+    iters = int(r.iters)
+    return dict(G=G, U=U, fit=float(r.fit), iters=iters,
+                fit_history=fh[:iters].cpu().numpy().tolist(),
+                rank_deficient=int(r.rank_deficient), bytes_streamed=float(moved.value))
+
+
+def tucker_sp_streamed(X: StreamTensor, J, C_raw, tol=1e-4, max_iter=50, out="device"):
+    return _run_streamed("tucker_sp_streamed", X, J, tol, max_iter, [None, None, C_raw], out)
+
+
+def tucker_mp_streamed(X: StreamTensor, J, tol=1e-4, max_iter=50, init=None, out="device"):
+    return _run_streamed("tucker_mp_streamed", X, J, tol, max_iter, init, out)

@@ -21,9 +21,12 @@ def test_autotune_decisions_and_reuse(tucker_lib):
     tk.tucker_autotune_enable(True)
     T = make(tk, (230, 210, 190), 90_000, 31)
     J = (36, 40, 44)                      # HOOI tiles of 64 columns: both TTMc variants apply
+    # modes above 256 rows: MP's mixed Grams take the projection kernels (smaller modes use the
+    # fused projection + Gram, which has no variants)
+    T2 = make(tk, (300, 280, 270), 200_000, 33)
     n0 = tk.tucker_autotune_count()
     r1 = tk.tucker_hooi(T, J, tol=-np.inf, max_iter=2, precision="mixed")
-    r1mp = tk.tucker_mp(T, J, tol=-np.inf, max_iter=2, precision="mixed")
+    r1mp = tk.tucker_mp(T2, J, tol=-np.inf, max_iter=2, precision="mixed")
     n1 = tk.tucker_autotune_count()
     assert n1 > n0
     fams = set()
@@ -35,7 +38,7 @@ def test_autotune_decisions_and_reuse(tucker_lib):
     assert fams == {1, 2}
     # the same shape classes again: no new decisions, identical results
     r2 = tk.tucker_hooi(T, J, tol=-np.inf, max_iter=2, precision="mixed")
-    r2mp = tk.tucker_mp(T, J, tol=-np.inf, max_iter=2, precision="mixed")
+    r2mp = tk.tucker_mp(T2, J, tol=-np.inf, max_iter=2, precision="mixed")
     assert tk.tucker_autotune_count() == n1
     assert r2["fit_history"] == r1["fit_history"] and r2mp["fit_history"] == r1mp["fit_history"]
     for a in range(3):

@@ -121,3 +121,24 @@ def test_gemm_empty_k(tucker_lib):
     A = torch.zeros((4, 0), dtype=torch.float64, device="cuda")
     B = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
     assert np.array_equal(tucker_lib.tucker_gemm(A, B).cpu().numpy(), np.zeros((4, 3)))
+
+
+# ---- the HOOI projection with its rank updates on the tensor cores ---------------------------
+
+@pytest.mark.parametrize("J", [(50, 60, 70), (33, 64, 100)])
+def test_ttmc_tensor_cores(tucker_lib, J):
+    # sizes above the dispatch threshold (J_m J_o >= 2048, >= 4096 fibers): every mode's
+    # projection runs as per-slice products on the tensor cores
+    X = synth.random_sparse_tensor((200, 150, 180), 200_000, synth.config_seed(970))
+    # empty slices of mode 0: rows of Y_(1) that must come out zero
+    keep = X.idx[0] % 9 != 4
+    idx, val = X.idx[:, keep], X.val[keep]
+    T = tucker_lib.tucker_tensor_create(idx, val, X.dims)
+    U = [synth.uniform_matrix(X.dims[a], J[a], 971 + a) - 0.5 for a in range(3)]
+    for n in range(3):
+        m, o = O.other_modes(n)
+        Y = tucker_lib.tucker_ttmc(T, n, U[m], U[o]).cpu().numpy()
+        ref = O.unfold_dense(O.ttmc(X.dims, idx, val, n, U), n)
+        assert rel_err(Y, ref) <= 1e-13, n
+    Y0 = tucker_lib.tucker_ttmc(T, 0, U[1], U[2]).cpu().numpy()
+    assert np.all(Y0[4::9] == 0.0)
