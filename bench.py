@@ -181,11 +181,15 @@ def run_step(tk, T, start, precision, out="device"):
     return {"hooi": h["fit"], "mp": m["fit"]}
 
 
-KERNELS = ("gram_f64_tc", "gram_ozaki", "gemm_ozaki", "ozaki_split", "syrk_f64", "gram_bf16x3", "ttmc_f64", "ttmc_mixed", "slice_proj_f64",
-           "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64", "gemm_nn_f32", "gemm_tn_f64",
-           "chol_f64", "jacobi_f64", "csf_build")
+KERNELS = ("gram_ozaki", "gemm_ozaki", "eig_mv_ozaki", "eig_tn_ozaki", "ttmc_ozaki",
+           "ozaki_split", "syrk_f64", "gram_bf16x3", "gram_fused", "ttmc_f64", "ttmc_mixed",
+           "slice_proj_f64", "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64", "gemm_nn_f32",
+           "gemm_tn_f64", "chol_f64", "jacobi_f64", "csf_build")
+# FP64 products on the BF16 tensor cores (their FLOPs are the BF16 FLOPs issued)
+OZAKI_KERNELS = ("gram_ozaki", "gemm_ozaki", "eig_mv_ozaki", "eig_tn_ozaki", "ttmc_ozaki")
 # spans that contain several of the kernels above
-STAGES = ("gram_f64_tc", "eig_topk", "syev_refined", "syev_jacobi32")
+STAGES = ("gram_f64_tc", "ttmc_f64_tc", "eig_topk", "eig_power", "eig_rr", "eig_lock",
+          "eig_filter", "eig_orth", "syev_refined", "syev_jacobi32")
 # eigensolver counters: iterations, and per solve its kernel launches and host synchronisations
 COUNTERS = ("eig_outer", "syev_steps", "syev_fp32_sweeps", "syev_fallback", "eig_launches",
             "eig_host_syncs")
@@ -674,10 +678,10 @@ def main():
                 "(the BF16x3 kernel issues 3x as many)")
     if dom == "gram_bf16x3":
         roofline = roofline_of(prof, dom, prof_ms, "tensor", bf16, "TFLOP/s", bf16_src)
-    elif dom == "gram_ozaki":
+    elif dom in OZAKI_KERNELS:
         roofline = roofline_of(prof, dom, prof_ms, "tensor", bf16, "TFLOP/s",
                                f"{peak_src} bf16 sustained (cuBLAS); BF16 FLOPs the tensor cores "
-                               "issue (28 slice products per FP64 product)")
+                               "issue (22 or 28 slice products per FP64 product)")
     else:
         roofline = roofline_of(prof, dom, prof_ms, "alu", FP64_PEAK_TFLOPS, "TFLOP/s", fp64_src)
     mx_gram = roofline_of(mx_prof, "gram_bf16x3", mx_prof_ms, "tensor", bf16, "TFLOP/s", bf16_src)

@@ -225,20 +225,21 @@ int tucker_slice_proj(tucker_tensor X, int32_t n, int32_t m, const double* d_Um,
 
 /* Gram M = Y1 Y1^T (+ Y2 Y2^T when d_Y2 != NULL): Y1 is rows x K1, Y2 rows x K2, row-major;
  * M is rows x rows (both triangles written).  Computed on the BF16 tensor cores to FP64
- * accuracy: every row is scaled by a power of two and cut into seven 7-bit integer slices
- * (error-free splitting, Ozaki et al. 2012); the 28 slice products that reach 2^-49 of the
- * leading term are summed exactly (integer-valued FP32 chunks, 64-bit integer totals), so the
- * error is a few units of 2^-49 |y_i| |y_j| per entry and the result does not depend on how K
- * is split.  d_Y1 may be NULL when K1 = 0 (M = 0).  ETIMEOUT if a bounded wait inside the
+ * accuracy: every row is scaled by a power of two and cut into six 8-bit integer slices
+ * (error-free splitting, Ozaki et al. 2012); the 22 slice products that reach 2^-47 of the
+ * leading term (with the one square pair of the next level, whose sum on the diagonal does not
+ * average out) are summed exactly (integer-valued FP32 chunks, 64-bit integer totals), so the
+ * error is a few units of 2^-47 max|y_i| max|y_j| per term (max over each row), zero on
+ * average, and the result does not depend on how K is split.  d_Y1 may be NULL when K1 = 0 (M = 0).  ETIMEOUT if a bounded wait inside the
  * kernel gave up. */
 int tucker_gram(const double* d_Y1, int64_t K1, const double* d_Y2, int64_t K2, int32_t rows,
                 double* d_M, void* stream);
 
 /* C = A B (A: m x K, ld lda; B: K x n, ld ldb; C: m x n, ld ldc; row-major, device), computed
  * on the BF16 tensor cores with the error-free slicing of tucker_gram: every row of A and every
- * column of B is scaled by a power of two and cut into seven 7-bit slices, so the error of
- * C[i][j] is a few units of 2^-49 max_k |A[i][k]| max_k |B[k][j]| (times sqrt(K) at most for
- * uncorrelated errors).  The eigensolver's products with M (M V) use it.  d_A, d_B may be NULL
+ * column of B is scaled by a power of two and cut into seven 8-bit slices (28 slice
+ * products), so the error of C[i][j] is a few units of 2^-55 max_k |A[i][k]| max_k |B[k][j]|
+ * (times sqrt(K) at most for uncorrelated errors).  The eigensolver's products with M (M V) use it.  d_A, d_B may be NULL
  * when K = 0 (C = 0). */
 int tucker_gemm(const double* d_A, int64_t lda, const double* d_B, int64_t ldb, int32_t m,
                 int32_t n, int64_t K, double* d_C, int64_t ldc, void* stream);

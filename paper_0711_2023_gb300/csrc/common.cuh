@@ -46,12 +46,14 @@ long long launch_count();
 // (tucker_profile_query reports the occurrences as launches and the sum of values as flops).
 void prof_count(const char* name, double value);
 
-// Records CUDA events around its lifetime on `s` when profiling is enabled
+// Records CUDA events around its lifetime (or up to end()) on `s` when profiling is enabled
 // (tucker_profile_enable), tagged with the launch's algorithmic FLOPs and bytes.
 class ProfScope {
  public:
   ProfScope(const char* name, cudaStream_t s, double flops, double bytes);
-  ~ProfScope();
+  ~ProfScope() { end(); }
+  // Closes the span now (the destructor then does nothing).
+  void end();
   ProfScope(const ProfScope&) = delete;
   ProfScope& operator=(const ProfScope&) = delete;
 

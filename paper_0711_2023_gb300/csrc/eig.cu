@@ -746,7 +746,7 @@ int op_mv(EigOps& e, const double* Mop, const float* Mop32, const double* V, int
     }
     TK_TRY(oz_split_cols(V, ldv, n, cols, OZ_GEMM_SLICES, &e.b, e.s));
     return oz_gemm_nt(e.msl, e.b, false, alpha, beta, X, ldx, gamma, Z, ldz, C, ldc, e.status,
-                      e.s, "gemm_ozaki");
+                      e.s, "eig_mv_ozaki");
   }
   return gemm_nn_f64(n, cols, n, alpha, Mop, n, V, ldv, beta, X, ldx, gamma, Z, ldz, C, ldc, e.s);
 }
@@ -758,10 +758,10 @@ int op_tn(EigOps& e, int ka, int kb, int64_t K, const double* A, int64_t lda, co
     TK_TRY(oz_split_cols(A, lda, K, ka, OZ_GEMM_SLICES, &e.a, e.s));
     if (A == B && lda == ldb && ka == kb)
       return oz_gemm_nt(e.a, e.a, true, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, C, ldc, e.status,
-                        e.s, "gemm_ozaki");
+                        e.s, "eig_tn_ozaki");
     TK_TRY(oz_split_cols(B, ldb, K, kb, OZ_GEMM_SLICES, &e.b, e.s));
     return oz_gemm_nt(e.a, e.b, false, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, C, ldc, e.status,
-                      e.s, "gemm_ozaki");
+                      e.s, "eig_tn_ozaki");
   }
   return gemm_tn_f64(ka, kb, K, A, lda, B, ldb, C, ldc, e.s);
 }
@@ -986,6 +986,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
   // full rank when M has fewer than k nonzero eigenvalues.  (A warm start with a single power
   // step costs more Rayleigh-Ritz iterations than the three steps it saves.)
   const int power_steps = 4;
+  ProfScope prof_power("eig_power", s, 0.0, 0.0);
   for (int rep = 0; rep < power_steps; ++rep) {
     double* W = T1.as<double>();
     TK_TRY(op_mv(ops, M, use32 ? M32 : nullptr, V, k, k, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, W,
@@ -1003,6 +1004,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     }
   }
 
+  prof_power.end();
   int nl = 0;
   double theta1 = 0.0;
   std::vector<double> locked_theta;
@@ -1016,6 +1018,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     double* Va = V + nl;
     double* W = T1.as<double>();
     // Rayleigh-Ritz on the active block.
+    ProfScope prof_rr("eig_rr", s, 0.0, 0.0);
     TK_TRY(op_mv(ops, M, nullptr, Va, k, ka, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, W, ka));
     st->matvecs++;
     TK_TRY(op_tn(ops, ka, ka, n, Va, k, W, ka, H.as<double>(), ka));
@@ -1044,6 +1047,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
       set_error_detail("eigensolver: a bounded wait in a tensor-core product gave up");
       return TUCKER_ETIMEOUT;
     }
+    prof_rr.end();
     theta1 = std::max(theta1, th[0]);
     const double thr = tol * std::max(theta1, 1e-300);
     int nlock = 0;
@@ -1057,6 +1061,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
       // Filter operator with the locked pairs removed: Md = M - L diag(theta_L) L^T.  Their
       // eigenvalues drop to ~0, inside the damped interval, so the filter needs no projection
       // at every step (only the final one below).
+      ProfScope prof_lock("eig_lock", s, 0.0, 0.0);
       TK_CUDA(cudaMemcpyAsync(lamd.p, locked_theta.data(), sizeof(double) * nl,
                               cudaMemcpyHostToDevice, s));
       scaled_transpose<<<ceil_div((int64_t)n * nl, 256), 256, 0, s>>>(V, k, n, nl,
@@ -1102,6 +1107,7 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
     for (int rep = 0; rep < reps; ++rep) {
       double* Y0 = T1.as<double>();
       double* Y1 = T2.as<double>();
+      ProfScope prof_filter("eig_filter", s, 0.0, 0.0);
       TK_TRY(copy_cols_f64(n, ka2, Xa, k, Y0, ka2, s));
       TK_TRY(op_mv(ops, Mf, use32 ? Mf32 : nullptr, Y0, ka2, ka2, 1.0 / e, -cc / e, Y0, ka2, 0.0,
                    nullptr, 0, Y1, ka2));
@@ -1114,6 +1120,8 @@ int eig_topk_f64(const double* M, int n, int J, const double* U0, double* U, dou
         double* t = Y0; Y0 = Y1; Y1 = t;
       }
       TK_TRY(copy_cols_f64(n, ka2, Y1, ka2, Xa, k, s));
+      prof_filter.end();
+      ProfScope prof_orth("eig_orth", s, 0.0, 0.0);
       for (int dd = 0; dd < 2; ++dd) TK_TRY(deflate(ops, V, k, Xa, k, n, nl, ka2, P.as<double>()));
       normalize_cols_inplace<<<ka2, 256, 0, s>>>(Xa, k, n);
       TK_LAUNCH();

@@ -7,27 +7,33 @@
 // products with M.
 //
 //   * every row i of an operand (a row of A, or a column of B for A B) is scaled by a power of
-//     two, u = y 2^-e_i with |u| < 1/2, and cut into S = 7 integer slices of 7 bits,
-//     u = sum_s q_s 2^(-7(s+1)) + r with |q_s| <= 64 and |r| <= 2^-50 (each q_s exact in BF16);
-//   * u_i . v_j = 2^-14 sum_d L_d 2^(-7d), with the level sums L_d = sum_{s+t=d} q_s(i).q_t(j)
-//     kept for d <= 6 (28 slice pairs); the dropped pairs and r contribute about 2^-49;
+//     two, u = y 2^-e_i with |u| < 1/2, and cut into S integer slices of 8 bits,
+//     u = sum_s q_s 2^(-8(s+1)) + r with |q_s| <= 128 and |r| <= 2^-(8S+1) (each q_s exact in
+//     BF16).  S = 6 (48 bits) for the Grams and the HOOI projection, S = 7 (56 bits) for the
+//     eigensolver's products, whose rows can be dominated by a single entry;
+//   * u_i . v_j = 2^-16 sum_d L_d 2^(-8d), with the level sums L_d = sum_{s+t=d} q_s(i).q_t(j)
+//     kept for d < S (S (S + 1) / 2 slice pairs).  For even S the first dropped level holds
+//     the square pair (S/2, S/2), whose products q_s(k)^2 on a Gram's diagonal do not average
+//     out: that one pair is kept as a level of its own (22 pairs for S = 6, 28 for S = 7).  The
+//     remaining dropped pairs (products of different digits, zero on average) and r contribute
+//     about 2^-(8S-1) per term;
 //   * each level has its own FP32 accumulator in tensor memory.  Its products are integers of
-//     at most 2^12, so a chunk of 256 K columns (levels 0..3) or 128 (levels 4..6) sums to at
-//     most 2^22 in magnitude and the FP32 accumulation is exact;
+//     at most 2^14, and a level is read out after at most 1024 / (d + 1) K columns, so every
+//     partial sum is an integer of at most 2^24 and the FP32 accumulation is exact;
 //   * the level chunks are read out on a staggered schedule (at most two levels per K stage,
 //     while the tensor pipe works on the others), converted to integers and summed in 64-bit
-//     integer registers: hi = sum_{d<=3} L_d 2^(7(3-d)), lo = sum_{d>=4} L_d 2^(7(6-d)).  The
+//     integer registers: hi = sum_{d<=3} L_d 2^(8(3-d)), lo = sum_{d>=4} L_d 2^(8(6-d)).  The
 //     integer sums are exact, so the result does not depend on the order of the K chunks;
 //   * a reduction kernel adds the K splits' integer partials, scales them back to FP64 and
 //     applies the epilogue alpha C + beta X + gamma Z.
 //
 // Layout: one CTA computes a 128 x 64 tile (rows of A = tile ti of 128 rows, rows of B^T =
 // tile tj of 64 rows; for a symmetric product only tj <= 2 ti + 1, the lower triangle) over a
-// range of K stages of 32 columns.  Warp 0 streams all 7 slices of A (128 x 32) and B (64 x 32)
-// of a stage with two 3-D TMA loads (64-byte swizzle) through a 2-stage ring; warp 1 issues
-// the 56 MMAs of a stage (M = 128, N = 64, K = 16, kind::f16); warps 2-9 read the level
-// accumulators out.  Every wait is bounded: on a timeout the kernel records DEV_TIMEOUT,
-// drains and returns.
+// range of K stages of 32 columns.  Warp 0 streams all S slices of A (128 x 32) and B (64 x 32)
+// of a stage with two 3-D TMA loads (64-byte swizzle) through a 3-stage (S = 6) or 2-stage
+// (S = 7) ring; warp 1 issues the 44 or 56 MMAs of a stage (M = 128, N = 64, K = 16,
+// kind::f16); warps 2-9 read the level accumulators out.  Every wait is bounded: on a timeout
+// the kernel records DEV_TIMEOUT, drains and returns.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -40,29 +46,59 @@ namespace tk {
 
 namespace {
 
-constexpr int BETA = 7;                              // bits per slice
-constexpr int TM = 128, TN = 64, KS = 32, STAGES = 2;
+constexpr int BETA = 8;                              // bits per slice
+constexpr int TM = 128, TN = 64, KS = 32;
 constexpr int NTHREADS = 320;                        // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr uint32_t IDESC = tc::idesc_bf16(TM, TN);
 
 // Ring geometry for S slices per operand (S levels, S (S + 1) / 2 slice pairs): one stage holds
-// all S slices of A (S x 8 KB) and of B (S x 4 KB); S <= 8 (8 levels x 64 columns = all of TMEM).
+// all S slices of A (S x 8 KB) and of B (S x 4 KB); 3 stages for S <= 6 (221 KB), else 2.
+// S <= 7: 7 levels x 64 columns fit in tensor memory, and 8 S bits fit the 64-bit split.
 template <int S>
 struct Geo {
+  static_assert(S >= 5 && S <= 7, "5 to 7 slices per operand");
   static constexpr int A_BYTES = S * TM * KS * 2;
   static constexpr int B_BYTES = S * TN * KS * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
+  static constexpr int NSTAGE = S <= 6 ? 3 : 2;
+  static constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 512;
+  // Levels: d < S, plus for even S a level S holding the one pair (S/2, S/2) (see the file
+  // comment); the lowest level is 6 for S = 6 and S = 7.
+  static constexpr int NL = S % 2 == 0 ? S + 1 : S;
+  static constexpr int PAIRS = S * (S + 1) / 2 + (S % 2 == 0 ? 1 : 0);
 };
+// Lowest level kept for nslice slices (the lo sum is scaled by 2^-8 LT).
+__host__ __device__ constexpr int oz_lowest_level(int nslice) {
+  return nslice % 2 == 0 ? nslice : nslice - 1;
+}
 
 // Readout schedule of level d: its accumulator restarts at local stage j > 0 when
-// j % CHUNK[d] == RESIDUE[d] (a chunk of CHUNK[d] stages of 32 columns at most).
-__host__ __device__ constexpr int level_chunk(int d) { return d <= 3 ? 8 : 4; }
-__host__ __device__ constexpr int level_residue(int d) {
-  return d == 0 ? 0 : d == 1 ? 6 : d == 2 ? 4 : d == 3 ? 2 : (d & 1) ? 3 : 1;
+// j % CHUNK[d] == RESIDUE[d].  A chunk spans at most CHUNK[d] stages of 32 columns, and
+// (d + 1) CHUNK[d] <= 32, so a chunk sums at most 32 x 32 products of magnitude <= 2^14: |L| <= 2^24,
+// every partial sum is an integer that FP32 holds exactly.  The residues spread the readouts
+// (at most two levels restart at one stage).
+__host__ __device__ constexpr int level_chunk(int d) {
+  return d == 0 ? 32 : d == 1 ? 16 : d <= 3 ? 8 : 4;
 }
+__host__ __device__ constexpr int level_residue(int d) {
+  return d == 0 ? 0 : d == 1 ? 8 : d == 2 ? 2 : d == 3 ? 6 : d == 4 ? 1 : d == 5 ? 3 : 0;
+}
+// Stages per K split or per batched job: at most 2^19 (2^24 columns), so that the integer
+// sums of a job, |hi| <= K 2^14 (2^24 + 2^17 + 3 2^8 + 4), stay below 2^63.
+constexpr int MAX_JOB_STAGES = 1 << 19;
 __device__ __forceinline__ bool restarts(int d, int j) {
   return j > 0 && j % level_chunk(d) == level_residue(d);
+}
+// Bit d set: level d restarts at local stage j (the chunks are powers of two).
+template <int S>
+__device__ __forceinline__ uint32_t restart_mask(int j) {
+  uint32_t m = 0;
+  if (j > 0) {
+#pragma unroll
+    for (int d = 0; d < Geo<S>::NL; ++d)
+      if ((j & (level_chunk(d) - 1)) == level_residue(d)) m |= 1u << d;
+  }
+  return m;
 }
 
 // Grid geometry: CTA b computes tile pair b % npairs over K split b / npairs.  Tile pairs are
@@ -121,11 +157,12 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                   const Grid grid, long long* __restrict__ partial, int* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int STAGES = Geo<S>::NSTAGE, NL = Geo<S>::NL, LT = NL - 1;
   uint64_t* full = (uint64_t*)(smem + STAGES * Geo<S>::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;   // [S] a level's chunk is complete in TMEM
-  uint64_t* acc_free = acc_full + S;     // [S] the epilogue has read it
-  uint64_t* done = acc_free + S;
+  uint64_t* acc_full = empty + STAGES;   // [NL] a level's chunk is complete in TMEM
+  uint64_t* acc_free = acc_full + NL;    // [NL] the epilogue has read it
+  uint64_t* done = acc_free + NL;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -137,7 +174,7 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    for (int d = 0; d < S; ++d) {
+    for (int d = 0; d < NL; ++d) {
       tc::mbar_init(&acc_full[d], 1);
       tc::mbar_init(&acc_free[d], 8);   // one arrival per epilogue warp
     }
@@ -182,12 +219,17 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
       // bytes / 16 (the whole ring lies below 256 KB, so the 14-bit field does not overflow).
       const uint64_t da0 = tc::sw_desc(st, 64), db0 = tc::sw_desc(st + Geo<S>::A_BYTES, 64);
       constexpr uint64_t DA = (TM * KS * 2) >> 4, DB = (TN * KS * 2) >> 4;
+      const uint32_t rm = restart_mask<S>(j);
+      const uint32_t fresh = j == 0 ? 0xFFFFu : rm;
       // Levels that keep accumulating first, then the restarting ones (their accumulators
-      // must first have been read out).
-      for (int pass = 0; pass < 2 && ok; ++pass) {
-        for (int d = 0; d < S; ++d) {
-          const bool rs = restarts(d, j);
-          if ((pass == 0) == rs) continue;
+      // must first have been read out).  Fully unrolled: the issuing thread spends a few
+      // instructions per MMA.
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+        for (int d = 0; d < NL; ++d) {
+          const bool rs = (rm >> d) & 1u;
+          if (pass == 0 ? rs : !rs) continue;
           if (rs) {
             if (!tc::mbar_wait(&acc_free[d], (free_phase >> d) & 1u, status, abort_flag)) {
               ok = false;
@@ -197,20 +239,27 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             tc::fence_after();
           }
           const uint32_t dt = tmem + (uint32_t)(d * TN);
-          const bool fresh = (j == 0) || rs;
+          const uint32_t acc0 = ((fresh >> d) & 1u) ? 0u : 1u;
 #pragma unroll
           for (int kk = 0; kk < KS / 16; ++kk) {
             const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
-            for (int q = 0; q <= d; ++q)
-              tc::mma_bf16<IDESC>(dt, da0 + q * DA + off, db0 + (d - q) * DB + off,
-                                  (fresh && kk == 0 && q == 0) ? 0u : 1u);
+            if (d < S) {
+#pragma unroll
+              for (int q = 0; q <= d; ++q)
+                tc::mma_bf16<IDESC>(dt, da0 + (q * DA + off), db0 + ((d - q) * DB + off),
+                                    (kk == 0 && q == 0) ? acc0 : 1u);
+            } else {   // level S: the pair (S/2, S/2) only
+              tc::mma_bf16<IDESC>(dt, da0 + ((S / 2) * DA + off), db0 + ((S / 2) * DB + off),
+                                  kk == 0 ? acc0 : 1u);
+            }
           }
         }
+        if (!ok) break;
       }
       if (!ok) break;
       tc::mma_commit(&empty[s]);
       const bool last = j + 1 == job.ns;
-      for (int d = 0; d < S; ++d)
+      for (int d = 0; d < NL; ++d)
         if (last || restarts(d, j + 1)) tc::mma_commit(&acc_full[d]);
     }
     tc::mma_commit(done);   // arrives once every MMA issued above has completed
@@ -236,11 +285,11 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
       tc::fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acc_free[d]);
-      // |L| <= 2^22: adding 1.5 * 2^23 puts the integer in the low mantissa bits.
-      const int sh = d <= 3 ? BETA * (3 - d) : BETA * (S - 1 - d);
+      // |L| <= 2^24 and integral: the conversion is exact.
+      const int sh = d <= 3 ? BETA * (3 - d) : BETA * (LT - d);
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
-        const int v = __float_as_int(__uint_as_float(r[i]) + 12582912.0f) - 0x4B400000;
+        const int v = __float2int_rn(__uint_as_float(r[i]));
         const long long w = (long long)v << sh;
         if (d <= 3)
           hi[i] += w;
@@ -249,10 +298,10 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
       }
     };
     for (int j = 1; j < job.ns && ok; ++j)
-      for (int d = 0; d < S; ++d)
+      for (int d = 0; d < NL; ++d)
         if (restarts(d, j)) readout(d);
     if (job.ns > 0)
-      for (int d = 0; d < S; ++d) readout(d);
+      for (int d = 0; d < NL; ++d) readout(d);
     if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
       const int row = q * 32 + lane;
       long long* ph = partial + (int64_t)blockIdx.x * 2 * TM * TN + (int64_t)row * TN + h * 32;
@@ -310,22 +359,22 @@ __device__ __forceinline__ long long oz_fixed(double y, int e) {
   return (b >> 63) ? -z : z;
 }
 
-// Cuts Z into S balanced base-128 digits, Z = sum_s q_s 128^(S-1-s) with q_(S-1)..q_1 in
-// [-64, 63] and |q_0| <= 64, and stores slice s (q_s as a BF16 integer) at out[s * plane].
+// Cuts Z into S balanced base-256 digits, Z = sum_s q_s 256^(S-1-s) with q_(S-1)..q_1 in
+// [-128, 127] and |q_0| <= 128, and stores slice s (q_s as a BF16 integer) at out[s * plane].
 template <int S>
 __device__ __forceinline__ void oz_cut(long long z, __nv_bfloat16* out, int64_t plane) {
   int q[S];
 #pragma unroll
   for (int s = S - 1; s > 0; --s) {
-    const int d = (int)((z + 64) & 127) - 64;
+    const int d = (int)((z + 128) & 255) - 128;
     q[s] = d;
-    z = (z - d) >> 7;                             // exact: z - d is a multiple of 128
+    z = (z - d) >> 8;                             // exact: z - d is a multiple of 256
   }
   q[0] = (int)z;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     __nv_bfloat16_raw r;
-    r.x = (unsigned short)(__float_as_uint((float)q[s]) >> 16);   // exact: at most 7 bits
+    r.x = (unsigned short)(__float_as_uint((float)q[s]) >> 16);   // exact: at most 8 bits
     out[s * plane] = r;
   }
 }
@@ -433,9 +482,9 @@ __global__ void oz_split_cols_kernel(const double* __restrict__ B, int64_t ldb, 
   }
 }
 
-// C[r][c] = alpha 2^(e_r + f_c - 14) (hi 2^-21 + lo 2^-7(S-1)) + beta X[r][c] + gamma Z[r][c],
-// with hi and lo summed over the K splits in integers.  A symmetric product fills r >= c and
-// mirrors.
+// C[r][c] = alpha 2^(e_r + f_c - 16) (hi 2^-24 + lo 2^-48) + beta X[r][c] + gamma Z[r][c],
+// with hi and lo summed over the K splits in integers (as high and low 32-bit halves, so that
+// many splits cannot overflow).  A symmetric product fills r >= c and mirrors.
 __global__ void oz_reduce(const long long* __restrict__ partial, const Grid g, int nslice, int m,
                           int n,
                           const int* __restrict__ exA, const int* __restrict__ exB, double alpha,
@@ -448,15 +497,19 @@ __global__ void oz_reduce(const long long* __restrict__ partial, const Grid g, i
   const int ti = r / TM, tj = c / TN;
   const int p = pair_index(g, ti, tj);
   const int rr = r - ti * TM, cc = c - tj * TN;
-  long long hi = 0, lo = 0;
+  long long hh = 0, hl = 0, lh = 0, ll = 0;
   for (int z = 0; z < g.nsplit; ++z) {
     const long long* P = partial + ((int64_t)z * g.npairs + p) * 2 * TM * TN;
-    hi += P[rr * TN + cc];
-    lo += P[TM * TN + rr * TN + cc];
+    const long long a = P[rr * TN + cc], b = P[TM * TN + rr * TN + cc];
+    hh += a >> 32;
+    hl += a & 0xFFFFFFFFll;
+    lh += b >> 32;
+    ll += b & 0xFFFFFFFFll;
   }
+  const double hi = ldexp((double)hh, 32) + (double)hl;
+  const double lo = ldexp((double)lh, 32) + (double)ll;
   const int E = exA[r] + exB[c] - 2 * BETA;
-  double v = alpha * (ldexp((double)hi, E - 3 * BETA) +
-                      ldexp((double)lo, E - (nslice - 1) * BETA));
+  double v = alpha * (ldexp(hi, E - 3 * BETA) + ldexp(lo, E - oz_lowest_level(nslice) * BETA));
   if (X) v += beta * X[(int64_t)r * ldx + c];
   if (Z) v += gamma * Z[(int64_t)r * ldz + c];
   C[(int64_t)r * ldc + c] = v;
@@ -503,7 +556,7 @@ int make_slice_map(CUtensorMap* m, const OzSlices& S, int box_rows) {
 }
 
 int reserve(OzSlices* out, int rows, int64_t ldK, int nslice, cudaStream_t s) {
-  if (nslice != 7 && nslice != 8) return TUCKER_EINVAL;
+  if (nslice != 6 && nslice != 7) return TUCKER_EINVAL;
   out->nslice = nslice;
   out->rows = rows;
   out->rows_pad = ceil_div(rows, TM) * TM;
@@ -532,7 +585,7 @@ int oz_split_rows(const double* A, int64_t lda, int rows, int64_t K1, const doub
   TK_LAUNCH();
   if (out->ldK == 0) return TUCKER_OK;   // no columns: nothing to cut
   const int64_t quads = (int64_t)out->rows_pad * (out->ldK / 4);
-  auto kern = nslice == 8 ? oz_split_rows_kernel<8> : oz_split_rows_kernel<7>;
+  auto kern = nslice == 7 ? oz_split_rows_kernel<7> : oz_split_rows_kernel<6>;
   kern<<<ceil_div(quads, 256), 256, 0, s>>>(rows, out->rows_pad, A, lda, K1, K1p, A2, lda2, K2,
                                             out->ldK, out->ex.as<int>(),
                                             out->Q.as<__nv_bfloat16>());
@@ -555,7 +608,7 @@ int oz_split_cols(const double* B, int64_t ldb, int64_t K, int cols, int nslice,
   oz_fix_zero_cols<<<ceil_div(cols, 256), 256, 0, s>>>(cols, out->ex.as<int>());
   TK_LAUNCH();
   if (out->ldK == 0) return TUCKER_OK;   // no rows of B: nothing to cut
-  auto kern = nslice == 8 ? oz_split_cols_kernel<8> : oz_split_cols_kernel<7>;
+  auto kern = nslice == 7 ? oz_split_cols_kernel<7> : oz_split_cols_kernel<6>;
   kern<<<dim3(out->rows_pad / 32, (unsigned)(out->ldK / 32)), dim3(32, 8), 0, s>>>(
       B, ldb, K, cols, out->rows_pad, out->ldK, out->ex.as<int>(), out->Q.as<__nv_bfloat16>());
   TK_LAUNCH();
@@ -588,11 +641,14 @@ int oz_gemm_nt(const OzSlices& A, const OzSlices& B, bool sym, double alpha, dou
   const int nst = (int)(A.ldK / KS);
   Grid g{ntj, 0, 1, nst, sym ? 1 : 0, nullptr};
   g.npairs = sym ? nti * (nti + 1) - (ntj < 2 * nti ? 1 : 0) : nti * ntj;
-  // K splits: the fewest that fill the SMs' waves to 90 %, each at least 8 stages long.
+  // K splits: the fewest that fill the SMs' waves to 90 %, each at least 8 stages long and at
+  // most MAX_JOB_STAGES.
   const int sms = num_sms();
-  const int max_split = std::max(1, std::min(64, nst / 8));
+  const int min_split = std::max(1, (nst + MAX_JOB_STAGES - 1) / MAX_JOB_STAGES);
+  const int max_split = std::max(min_split, std::min(64, nst / 8));
   double best = 0.0;
-  for (int z = 1; z <= max_split; ++z) {
+  g.nsplit = min_split;
+  for (int z = min_split; z <= max_split; ++z) {
     const int64_t jobs = (int64_t)g.npairs * z;
     const double eff = (double)jobs / (double)(((jobs + sms - 1) / sms) * sms);
     if (eff > best + 1e-9) {
@@ -622,13 +678,14 @@ int oz_gemm_nt(const OzSlices& A, const OzSlices& B, bool sym, double alpha, dou
   {
     // flops: the BF16 tensor-core FLOPs issued (S (S + 1) / 2 slice pairs per output tile and
     // K column); bytes: the slices read once plus the integer partials written.
-    ProfScope pk(prof_name, s, 2.0 * (S * (S + 1) / 2) * TM * TN * (double)KS * nst * g.npairs,
+    const int pairs = S * (S + 1) / 2 + (S % 2 == 0 ? 1 : 0);
+    ProfScope pk(prof_name, s, 2.0 * pairs * TM * TN * (double)KS * nst * g.npairs,
                  2.0 * S * ((double)A.rows_pad + (sym ? 0.0 : (double)B.rows_pad)) * A.ldK +
                      16.0 * TM * TN * (double)njobs);
-    if (S == 8)
-      TK_TRY(launch_products<8>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
-    else
+    if (S == 7)
       TK_TRY(launch_products<7>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
+    else
+      TK_TRY(launch_products<6>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
   }
   oz_reduce<<<ceil_div((int64_t)m * n, 256), 256, 0, s>>>(part.as<long long>(), g, S, m, n,
                                                            A.ex.as<int>(), B.ex.as<int>(), alpha,
@@ -706,7 +763,7 @@ __global__ void oz_split_gather_kernel(const double* __restrict__ Src, int64_t l
   }
 }
 
-// Y[i, p J_o + q] = 2^(ex_a[p] + ex_b[q] - 14) (hi 2^-21 + lo 2^-7(S-1)) of slice i's product.
+// Y[i, p J_o + q] = 2^(ex_a[p] + ex_b[q] - 16) (hi 2^-24 + lo 2^-48) of slice i's product.
 __global__ void oz_reduce_batched(const long long* __restrict__ partial, int ntj, int npairs,
                                   int nslice, int64_t nslices, int Jm, int Jo,
                                   const int* __restrict__ exA, const int* __restrict__ exB,
@@ -721,7 +778,7 @@ __global__ void oz_reduce_batched(const long long* __restrict__ partial, int ntj
   const int rr = p - ti * TM, cc = q - tj * TN;
   const long long hi = P[rr * TN + cc], lo = P[TM * TN + rr * TN + cc];
   const int E = exA[p] + exB[q] - 2 * BETA;
-  Y[t] = ldexp((double)hi, E - 3 * BETA) + ldexp((double)lo, E - (nslice - 1) * BETA);
+  Y[t] = ldexp((double)hi, E - 3 * BETA) + ldexp((double)lo, E - oz_lowest_level(nslice) * BETA);
 }
 
 // Padded K layout of a TTMc ordering: pad[i] = (stage start of slice i) * 32 - root_ptr[i],
@@ -753,7 +810,7 @@ int split_gather(const double* Src, int64_t ld, int J, const int32_t* rows, int6
 int ttmc_f64_tc(const tucker_tensor_s* X, const Ordering* o, const double* Um, int Jm,
                 const double* Uo, int Jo, double* Y, cudaStream_t s) {
   const int64_t In = X->dims[o->n], F = o->F;
-  const int S = OZ_GRAM_SLICES;
+  constexpr int S = OZ_GRAM_SLICES;
   if (In == 0) return TUCKER_OK;
   ProfScope prof("ttmc_f64_tc", s, 2.0 * ((double)X->nnz * Jo + (double)F * Jm * Jo),
                  12.0 * X->nnz + 16.0 * F + 8.0 * In * (double)Jm * Jo);
@@ -824,9 +881,10 @@ int ttmc_f64_tc(const tucker_tensor_s* X, const Ordering* o, const double* Um, i
   TK_TRY(make_slice_map(&mapA, A, TM));
   TK_TRY(make_slice_map(&mapB, B, TN));
   {
-    ProfScope pk("gemm_ozaki", s, 2.0 * 28.0 * TM * TN * (double)KS * stages * g.npairs,
+    ProfScope pk("ttmc_ozaki", s,
+                 2.0 * Geo<S>::PAIRS * TM * TN * (double)KS * stages * g.npairs,
                  2.0 * S * ((double)A.rows_pad + B.rows_pad) * ldK + 16.0 * TM * TN * (double)njobs);
-    TK_TRY(launch_products<7>(mapA, mapB, g, njobs, part.as<long long>(), st.as<int>(), s));
+    TK_TRY(launch_products<S>(mapA, mapB, g, njobs, part.as<long long>(), st.as<int>(), s));
   }
   oz_reduce_batched<<<ceil_div(In * Jm * Jo, 256), 256, 0, s>>>(
       part.as<long long>(), ntj, g.npairs, S, In, Jm, Jo, A.ex.as<int>(), B.ex.as<int>(), Y);

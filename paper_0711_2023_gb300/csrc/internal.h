@@ -113,19 +113,19 @@ int ttmc_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int
 int slice_proj_mixed(const tucker_tensor_s* X, const Ordering* o, const float* Um, int64_t ldm,
                      int Jm, __nv_bfloat16* Yh, __nv_bfloat16* Yl, int64_t ldY, cudaStream_t s);
 
-// gram_ozaki.cu: FP64-accurate products on the BF16 tensor cores (error-free 7-slice splitting,
-// exact integer level sums).  An operand is first cut into OzSlices: seven BF16 planes of a
-// K-major (rows_pad x ldK) matrix and one scale exponent per row.
-// nslice = 7 keeps 49 bits of every row's largest entry (error about 2^-49 max|a_i| max|b_j| per
-// term); nslice = 8 keeps 56 bits, for products whose rows are dominated by one entry and whose
+// gram_ozaki.cu: FP64-accurate products on the BF16 tensor cores (error-free splitting into
+// 8-bit slices, exact integer level sums).  An operand is first cut into OzSlices: nslice BF16
+// planes of a K-major (rows_pad x ldK) matrix and one scale exponent per row.
+// nslice = 6 keeps 48 bits of every row's largest entry (error about 2^-47 max|a_i| max|b_j| per
+// term); nslice = 7 keeps 56 bits, for products whose rows are dominated by one entry and whose
 // small terms must stay accurate (the eigensolver's M V: M is strongly diagonal-dominant).
 struct OzSlices {
   Buf Q, ex;
-  int nslice = 7;
+  int nslice = 6;
   int rows = 0, rows_pad = 0;
   int64_t ldK = 0;
 };
-constexpr int OZ_GRAM_SLICES = 7, OZ_GEMM_SLICES = 8;
+constexpr int OZ_GRAM_SLICES = 6, OZ_GEMM_SLICES = 7;
 int64_t oz_ldk(int64_t K);
 // Slices of the rows of [A | A2] (A: rows x K1, ld lda; A2 optional: rows x K2, ld lda2).
 int oz_split_rows(const double* A, int64_t lda, int rows, int64_t K1, const double* A2,

@@ -64,8 +64,9 @@ void prof_count(const char* name, double value) {
   g_recs.push_back(Rec{name, nullptr, nullptr, value, 0.0});
 }
 
-ProfScope::~ProfScope() {
+void ProfScope::end() {
   if (!active_) return;
+  active_ = false;
   cudaEventRecord(b_, s_);
   std::lock_guard<std::mutex> lk(g_mu);
   g_recs.push_back(Rec{name_, a_, b_, flops_, bytes_});

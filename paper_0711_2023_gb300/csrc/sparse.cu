@@ -301,8 +301,10 @@ int ttmc_f64_roots(int64_t nroots, const int64_t* root_ptr, const int32_t* fiber
 int ttmc_fp64(const tucker_tensor_s* X, const Ordering* o, const double* Um, int Jm,
               const double* Uo, int Jo, double* Y, cudaStream_t s) {
   // The rank-J_m J_o updates of the fibers dominate; with enough of them they run as per-slice
-  // products on the tensor cores (FP64-accurate), else on the CUDA cores.
-  if ((int64_t)Jm * Jo >= 2048 && o->F >= 4096) return ttmc_f64_tc(X, o, Um, Jm, Uo, Jo, Y, s);
+  // products on the tensor cores (FP64-accurate), else on the CUDA cores.  A slice holds at
+  // most I_m fibers; the tensor-core products take at most 2^24 per slice.
+  if ((int64_t)Jm * Jo >= 2048 && o->F >= 4096 && X->dims[o->m] <= (1 << 24))
+    return ttmc_f64_tc(X, o, Um, Jm, Uo, Jo, Y, s);
   return ttmc_f64(X, o, Um, Jm, Uo, Jo, Y, s);
 }
 

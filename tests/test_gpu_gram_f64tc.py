@@ -4,7 +4,9 @@ through tucker_gram, and the general product of the eigensolver, through tucker_
 
 Pins independent of the library: integer-valued inputs, whose slices hold every bit, must give
 the exact integer Gram bit for bit (a single inexact FP32 accumulation in the tensor cores, or a
-wrong slice pair, level weight or scale, breaks it); real inputs must match the FP64 product
+wrong slice pair, level weight or scale, breaks it); inputs whose slice digits are all at their
+largest magnitude must give the exact sum of the kept slice products (computed in rationals),
+which pins the FP32 accumulators at their 2^24 bound; real inputs must match the FP64 product
 within 1e-13 of max |M| over ragged tiles, one and two terms, zero rows, rows whose magnitudes
 differ by 2^200, and a K long enough to be split across CTAs."""
 import numpy as np
@@ -72,6 +74,68 @@ def test_long_k_split(tucker_lib):
     # the same Gram from two half-width terms (different K split points): equal within rounding
     M2 = tucker_lib.tucker_gram(Y[:, :K // 2].copy(), Y[:, K // 2:].copy()).cpu().numpy()
     assert rel_err(M2, M) <= 1e-14
+
+
+def _digit_value(digits):
+    """The value with these 8-bit slices at scale exponent 0: Z 2^-(8 S),
+    Z = sum_s q_s 256^(S-1-s) (exact in FP64 when Z has at most 53 significant bits)."""
+    from fractions import Fraction
+    S = len(digits)
+    Z = sum(d * 256 ** (S - 1 - s) for s, d in enumerate(digits))
+    y = Fraction(Z, 2 ** (8 * S))
+    assert float(y) == y
+    return float(y)
+
+
+def _kept_pairs(S):
+    """The slice pairs the tensor-core product sums: s + t < S, and for even S the square pair
+    (S/2, S/2) of level S."""
+    pairs = [(s, t) for s in range(S) for t in range(S) if s + t < S]
+    return pairs + ([(S // 2, S // 2)] if S % 2 == 0 else [])
+
+
+def _kept_sum(qa, qb):
+    """sum over the kept pairs of qa_s qb_t 2^-(8 (s + t + 2)), exactly."""
+    from fractions import Fraction
+    return sum(Fraction(qa[s] * qb[t], 2 ** (8 * (s + t + 2))) for s, t in _kept_pairs(len(qa)))
+
+
+def _max_digit_columns(K, qa, qb):
+    """Columns with slices qa, except every 16th with qb: with qa odd and qb even, every
+    16-column MMA step adds an odd number to each level, so a dropped low bit shows."""
+    ya, yb = _digit_value(qa), _digit_value(qb)
+    is_b = np.arange(K) % 16 == 0
+    return np.where(is_b, yb, ya), int(is_b.sum())
+
+
+def test_max_digit_accumulation_exact(tucker_lib):
+    # Slice digits near their largest magnitude (127, and 126 in every 16th column) and every
+    # row of one sign, so each level's FP32 accumulator climbs to just below 2^24 before it is
+    # read out: a rounding in the tensor cores' accumulation, or a readout chunk one stage too
+    # long, moves a level sum and the result.  K spans several level-0 chunks (1024 columns)
+    # and a ragged stage.  Expected: the exact sum of the kept slice products, in rationals.
+    qa, qb = [127] * 6, [126] * 6
+    K = 4 * 1024 + 77
+    row, nb = _max_digit_columns(K, qa, qb)
+    sign = np.array([1.0, -1.0, 1.0, 1.0, -1.0])
+    M = tucker_lib.tucker_gram(np.outer(sign, row)).cpu().numpy()
+    T = float((K - nb) * _kept_sum(qa, qa) + nb * _kept_sum(qb, qb))
+    ref = np.outer(sign, sign) * T
+    assert np.all(np.abs(M - ref) <= 2.0 * np.spacing(T)), (M[0, 0], T)
+
+
+def test_gemm_max_digit_accumulation_exact(tucker_lib):
+    # The same for the 7-slice product of tucker_gemm (last digit 124: the values stay within
+    # 53 bits).
+    qa, qb = [127] * 6 + [124], [126] * 6 + [124]
+    K = 2 * 1024 + 45
+    col, nb = _max_digit_columns(K, qa, qb)
+    A = np.outer(np.array([1.0, -1.0, 1.0]), col)
+    B = np.outer(col, np.ones(2))
+    C = tucker_lib.tucker_gemm(A, B).cpu().numpy()
+    T = float((K - nb) * _kept_sum(qa, qa) + nb * _kept_sum(qb, qb))
+    ref = np.array([[T, T], [-T, -T], [T, T]])
+    assert np.all(np.abs(C - ref) <= 2.0 * np.spacing(T)), (C[0, 0], T)
 
 
 def test_empty_k(tucker_lib):
