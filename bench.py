@@ -191,8 +191,8 @@ OZAKI_KERNELS = ("gram_ozaki", "gemm_ozaki", "eig_mv_ozaki", "eig_tn_ozaki", "tt
 STAGES = ("gram_f64_tc", "ttmc_f64_tc", "eig_topk", "eig_power", "eig_rr", "eig_lock",
           "eig_filter", "eig_orth", "syev_refined", "syev_jacobi32")
 # eigensolver counters: iterations, and per solve its kernel launches and host synchronisations
-COUNTERS = ("eig_outer", "syev_steps", "syev_fp32_sweeps", "syev_fallback", "eig_launches",
-            "eig_host_syncs")
+COUNTERS = ("eig_outer", "syev_steps", "syev_fp32_sweeps", "syev_cluster_rotations",
+            "syev_rotation_unconverged", "syev_fallback", "eig_launches", "eig_host_syncs")
 
 
 def timed_region(tk, torch, world, local, steps, T, start, l2buf, precision, profile=False):

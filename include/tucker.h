@@ -314,15 +314,21 @@ int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const dou
  * algorithmic FLOPs and bytes (what the method must compute and move, not what the kernel
  * happens to do).  Timed records: "gram_f64_tc" (the whole FP64 Gram: splitting, tensor-core
  * products, reduction) with its kernels "ozaki_split" and "gram_ozaki" (flops: the BF16 FLOPs
- * its tensor cores issue), "gemm_ozaki" (the eigensolver's FP64 products on the tensor cores,
- * flops likewise), the kernels "syrk_f64", "gram_bf16x3", "ttmc_f64",
+ * its tensor cores issue), "gemm_ozaki" (tucker_gemm's tensor-core products, flops likewise),
+ * "eig_mv_ozaki" and "eig_tn_ozaki" (the eigensolver's products M V and A^T B on the tensor
+ * cores), "ttmc_f64_tc" (the FP64 HOOI projection with its rank updates on the tensor cores)
+ * with its kernel "ttmc_ozaki", the kernels "syrk_f64", "gram_bf16x3", "gram_fused", "ttmc_f64",
  * "ttmc_mixed", "slice_proj_f64", "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64",
  * "gemm_nn_f32", "gemm_tn_f64", "chol_f64", "jacobi_f64", "csf_build", and the stages
- * "eig_topk" (one leading-eigenvector solve) and "syev_refined" (one small eigenproblem) with
+ * "eig_topk" (one leading-eigenvector solve: "eig_power" its initial power steps, "eig_rr" its
+ * Rayleigh-Ritz solves, "eig_lock" its deflation updates, "eig_filter" its Chebyshev filters,
+ * "eig_orth" its re-orthonormalisations) and "syev_refined" (one small eigenproblem) with
  * "syev_jacobi32" (its FP32 Jacobi).
  * Counters (occurrences as launches, summed values as flops, no time): "syev_steps" (value:
  * refinement steps of one small eigenproblem), "syev_fp32_sweeps" (value: sweeps of its FP32
- * Jacobi), "syev_fallback" (value 1: unresolved cluster,
+ * Jacobi), "syev_cluster_rotations" (value 1: near-degenerate clusters split by Jacobi
+ * rotations inside the refinement), "syev_rotation_unconverged" (value 1: those rotations hit
+ * their round limit before a fallback), "syev_fallback" (value 1: unresolved cluster,
  * 2: step limit, 3: order above the shared-memory limit), "eig_outer" (value: Rayleigh-Ritz
  * iterations of one solve), "eig_launches" and "eig_host_syncs" (value: the kernel launches and
  * host synchronisations of one solve).  Every name and the argument order are fixed; unknown names

@@ -295,6 +295,128 @@ oa_column_kernel(const double* __restrict__ SG, int m, int64_t ld, const double*
   }
 }
 
+// Jacobi rotations for the pairs a first-order refinement step cannot split (near-degenerate
+// clusters of eigenvalues).  B = 0.5 (S + S^T) with S = X^T A X (m x m, ld lds) is held in
+// shared memory; X (m x m, ld ldx) is rotated in place.  Each round: every thread scans its
+// share of B's strict upper triangle for entries above thr_rel * max |b_ii| (magnitudes compared
+// as bit patterns, off the FP64 pipe) that are not small against their diagonal gap
+// (|b_pq| > 0.05 |b_qq - b_pp|; the refinement's first-order step resolves the others); one
+// thread picks disjoint pairs greedily; their
+// symmetric Schur rotations (Golub & Van Loan, Algorithm 8.4.1) are applied to the rows of B,
+// then to its columns and to the columns of X, and the rotated entries are set to zero.  The
+// loop ends after a round without such an entry (info[0] = rounds, info[1] = 1) or after
+// max_rounds (info[1] = 0).  The clusters are small, so a round touches a few rows of B only.
+constexpr int ROT_MAX_CAND = 512;
+__global__ void __launch_bounds__(512)
+cluster_rotate_kernel(const double* __restrict__ S, int64_t lds, int m, double thr_rel,
+                      int max_rounds, double* __restrict__ X, int64_t ldx, int* __restrict__ info) {
+  extern __shared__ double b[];   // m x m
+  __shared__ int cp[ROT_MAX_CAND], cq[ROT_MAX_CAND];
+  __shared__ int sp[SYEV_REFINED_MAX_M / 2], sq[SYEV_REFINED_MAX_M / 2];
+  __shared__ double sc[SYEV_REFINED_MAX_M / 2], ss[SYEV_REFINED_MAX_M / 2];
+  __shared__ unsigned char used[SYEV_REFINED_MAX_M];
+  __shared__ int ncand, nsel;
+  __shared__ unsigned long long dmax_s;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) dmax_s = 0ull;
+  __syncthreads();
+  unsigned long long mb = 0ull;
+  for (int t = tid; t < m * m; t += nt) {
+    const int i = t / m, j = t - i * m;
+    const double v = 0.5 * (S[(int64_t)i * lds + j] + S[(int64_t)j * lds + i]);
+    b[t] = v;
+    if (i == j) {
+      const unsigned long long a = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+      mb = a > mb ? a : mb;
+    }
+  }
+  atomicMax(&dmax_s, mb);
+  __syncthreads();
+  const unsigned long long thr_bits = (unsigned long long)__double_as_longlong(
+      thr_rel * __longlong_as_double((long long)dmax_s));
+  int round = 0, done = 0;
+  for (; round < max_rounds; ++round) {
+    if (tid == 0) ncand = 0;
+    __syncthreads();
+    for (int t = tid; t < m * m; t += nt) {
+      const int i = t / m, j = t - i * m;
+      if (j <= i) continue;
+      const unsigned long long a = (unsigned long long)__double_as_longlong(b[t]) & 0x7fffffffffffffffull;
+      // pairs a first-order step resolves (|b_pq| <= 0.1 |b_qq - b_pp|) are left to it
+      if (a > thr_bits && fabs(b[t]) > 0.05 * fabs(b[j * m + j] - b[i * m + i])) {
+        const int c = atomicAdd(&ncand, 1);
+        if (c < ROT_MAX_CAND) {
+          cp[c] = i;
+          cq[c] = j;
+        }
+      }
+    }
+    __syncthreads();
+    if (ncand == 0) {   // uniform: read after the barrier
+      done = 1;
+      break;
+    }
+    if (tid == 0) {
+      for (int i = 0; i < m; ++i) used[i] = 0;
+      int n = 0;
+      const int nc = min(ncand, ROT_MAX_CAND);
+      for (int c = 0; c < nc && n < SYEV_REFINED_MAX_M / 2; ++c) {
+        const int p = cp[c], q = cq[c];
+        if (used[p] || used[q]) continue;
+        used[p] = used[q] = 1;
+        sp[n] = p;
+        sq[n] = q;
+        ++n;
+      }
+      nsel = n;
+    }
+    __syncthreads();
+    const int ns = nsel;
+    if (tid < ns) {
+      const int p = sp[tid], q = sq[tid];
+      const double apq = b[p * m + q];
+      const double tau = (b[q * m + q] - b[p * m + p]) / (2.0 * apq);
+      const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      const double c = 1.0 / sqrt(1.0 + t * t);
+      sc[tid] = c;
+      ss[tid] = t * c;
+    }
+    __syncthreads();
+    for (int t = tid; t < ns * m; t += nt) {   // rows p, q of B <- J^T B
+      const int r = t / m, k = t - r * m;
+      const int p = sp[r], q = sq[r];
+      const double c = sc[r], sn = ss[r];
+      const double bp = b[p * m + k], bq = b[q * m + k];
+      b[p * m + k] = c * bp - sn * bq;
+      b[q * m + k] = sn * bp + c * bq;
+    }
+    __syncthreads();
+    for (int t = tid; t < ns * m; t += nt) {   // columns p, q of B <- B J, and of X <- X J
+      const int r = t / m, k = t - r * m;
+      const int p = sp[r], q = sq[r];
+      const double c = sc[r], sn = ss[r];
+      const double bp = b[k * m + p], bq = b[k * m + q];
+      b[k * m + p] = c * bp - sn * bq;
+      b[k * m + q] = sn * bp + c * bq;
+      double* xr = X + (int64_t)k * ldx;
+      const double xp = xr[p], xq = xr[q];
+      xr[p] = c * xp - sn * xq;
+      xr[q] = sn * xp + c * xq;
+    }
+    __syncthreads();
+    if (tid < ns) {
+      const int p = sp[tid], q = sq[tid];
+      b[p * m + q] = 0.0;
+      b[q * m + p] = 0.0;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    info[0] = round;
+    info[1] = done;
+  }
+}
+
 }  // namespace
 
 int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* evals_out,
@@ -318,7 +440,7 @@ int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* eval
   TK_TRY(WX1.alloc(sizeof(double) * m * ld, s));
   TK_TRY(SG.alloc(sizeof(double) * m * ld, s));
   TK_TRY(E.alloc(sizeof(double) * m * m, s));
-  TK_TRY(misc.alloc(sizeof(double) * (4 * (size_t)m + 1), s));
+  TK_TRY(misc.alloc(sizeof(double) * (4 * (size_t)m + 2), s));
   double* stats = misc.as<double>();
   double* lam = stats + 3 * m;
   int* info = reinterpret_cast<int*>(lam + m);
@@ -339,12 +461,13 @@ int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* eval
   // Refinement.  The statistics are read back (one host synchronisation each) from the step
   // `first_check` on: from an FP32 start two steps rarely, and three steps usually, meet the
   // bars, so checking from step 3 needs one synchronisation in the common case.
-  const int max_steps = 6;
+  const int max_steps = 8;
   const int first_check = 3;
   const double bad_rel = acc_rel;
-  std::vector<double> hs(4 * (size_t)m + 1);
+  std::vector<double> hs(4 * (size_t)m + 2);
   int hinfo[2] = {0, 0};
   bool accepted = false, cluster = false;
+  int rotations = 0;
   int step = 0;
   for (; step <= max_steps; ++step) {
     double* X = cur + m;
@@ -374,10 +497,32 @@ int syev_refined(const double* A, int m, int64_t lda, double* Qout, double* eval
         accepted = true;
         break;
       }
-      // An unresolved cluster that matters does not get better by more first-order steps.
-      if (bad > 0.0 && step >= first_check + 1) {
-        cluster = true;
-        break;
+      // An unresolved cluster that matters does not get better by more first-order steps: its
+      // pairs are rotated by Jacobi on S = X^T A X (at most twice; the rotations are orthogonal,
+      // so X keeps its orthogonality error, which the following steps remove), and the
+      // refinement goes on from the rotated X.  If that does not settle it, the FP64 Jacobi
+      // takes over.
+      if (bad > 0.0) {
+        if (rotations == 2 || orth > 1e-4) {
+          if (rotations > 0) {
+            int rinfo[2];
+            memcpy(rinfo, hs.data() + 4 * m + 1, sizeof(rinfo));
+            prof_count("syev_rotation_unconverged", rinfo[1] ? 0.0 : 1.0);
+          }
+          cluster = true;
+          break;
+        }
+        ++rotations;
+        const size_t rsm = sizeof(double) * (size_t)m * m;
+        static const cudaError_t rattr = cudaFuncSetAttribute(
+            cluster_rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)(sizeof(double) * SYEV_REFINED_MAX_M * SYEV_REFINED_MAX_M));
+        TK_CUDA(rattr);
+        cluster_rotate_kernel<<<1, 512, rsm, s>>>(SG.as<double>(), ld, m, 0.25 * acc_rel, 4 * m,
+                                                  X, ld, info + 2);
+        TK_LAUNCH();
+        prof_count("syev_cluster_rotations", 1.0);
+        continue;
       }
     }
     if (step == max_steps) break;

@@ -133,7 +133,15 @@ def test_eig_topk_clusters_and_outlier(tucker_lib, n):
                         np.linspace(2.5, 1.0, J - 8), 0.1 * np.linspace(1.0, 0.0, n - J)])
     M = (Q * w) @ Q.T
     M = 0.5 * (M + M.T)
+    tucker_lib.tucker_profile_enable(True)
     U, lam = tucker_lib.tucker_eig_topk(M, J)
+    rot = tucker_lib.tucker_profile_query("syev_cluster_rotations")[0]
+    fb = tucker_lib.tucker_profile_query("syev_fallback")[0]
+    tucker_lib.tucker_profile_enable(False)
+    if n == 120:
+        # all eigenpairs of M by one small eigenproblem: its clusters are split by the Jacobi
+        # rotations inside the refinement, without the FP64 Jacobi fallback
+        assert rot >= 1 and fb == 0, (rot, fb)
     U, lam = U.cpu().numpy(), lam.cpu().numpy()
     V, wr = O.leading_eigvecs(M, J)
     np.testing.assert_allclose(lam, wr[:J], rtol=1e-11, atol=1e-12 * wr[0])
