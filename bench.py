@@ -181,12 +181,13 @@ def run_step(tk, T, start, precision, out="device"):
     return {"hooi": h["fit"], "mp": m["fit"]}
 
 
-KERNELS = ("gram_ozaki", "gemm_ozaki", "eig_mv_ozaki", "eig_tn_ozaki", "ttmc_ozaki",
-           "ozaki_split", "syrk_f64", "gram_bf16x3", "gram_fused", "ttmc_f64", "ttmc_mixed",
-           "slice_proj_f64", "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64", "gemm_nn_f32",
-           "gemm_tn_f64", "chol_f64", "jacobi_f64", "csf_build")
+KERNELS = ("gram_ozaki", "gemm_ozaki", "eig_mv_ozaki", "eig_mv_ozaki3", "eig_tn_ozaki",
+           "ttmc_ozaki", "ozaki_split", "syrk_f64", "gram_bf16x3", "gram_fused", "ttmc_f64",
+           "ttmc_mixed", "slice_proj_f64", "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64",
+           "gemm_nn_f32", "gemm_tn_f64", "chol_f64", "jacobi_f64", "csf_build")
 # FP64 products on the BF16 tensor cores (their FLOPs are the BF16 FLOPs issued)
-OZAKI_KERNELS = ("gram_ozaki", "gemm_ozaki", "eig_mv_ozaki", "eig_tn_ozaki", "ttmc_ozaki")
+OZAKI_KERNELS = ("gram_ozaki", "gemm_ozaki", "eig_mv_ozaki", "eig_mv_ozaki3", "eig_tn_ozaki",
+                 "ttmc_ozaki")
 # spans that contain several of the kernels above
 STAGES = ("gram_f64_tc", "ttmc_f64_tc", "eig_topk", "eig_power", "eig_rr", "eig_lock",
           "eig_filter", "eig_orth", "syev_refined", "syev_jacobi32")

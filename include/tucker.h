@@ -316,7 +316,7 @@ int tucker_core(tucker_tensor X, const double* d_A, const double* d_B, const dou
  * products, reduction) with its kernels "ozaki_split" and "gram_ozaki" (flops: the BF16 FLOPs
  * its tensor cores issue), "gemm_ozaki" (tucker_gemm's tensor-core products, flops likewise),
  * "eig_mv_ozaki" and "eig_tn_ozaki" (the eigensolver's products M V and A^T B on the tensor
- * cores), "ttmc_f64_tc" (the FP64 HOOI projection with its rank updates on the tensor cores)
+ * cores), "eig_mv_ozaki3" (the mixed form's FP32-class filter products M V, 3 slices), "ttmc_f64_tc" (the FP64 HOOI projection with its rank updates on the tensor cores)
  * with its kernel "ttmc_ozaki", the kernels "syrk_f64", "gram_bf16x3", "gram_fused", "ttmc_f64",
  * "ttmc_mixed", "slice_proj_f64", "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64",
  * "gemm_nn_f32", "gemm_tn_f64", "chol_f64", "jacobi_f64", "csf_build", and the stages

@@ -724,18 +724,33 @@ constexpr double OZ_MIN_FLOPS = 2e7;
 struct EigOps {
   cudaStream_t s = 0;
   int n = 0;
-  const double* mop = nullptr;   // operator whose row slices are in msl (nullptr: none)
-  OzSlices msl, a, b;
-  int* status = nullptr;         // device word: DEV_TIMEOUT from the tensor-core kernels
-  void invalidate() { mop = nullptr; }
+  const double* mop = nullptr;    // operator whose row slices are in msl (nullptr: none)
+  const double* mop3 = nullptr;   // operator whose 3-slice row slices are in msl3
+  OzSlices msl, msl3, a, b;
+  int* status = nullptr;          // device word: DEV_TIMEOUT from the tensor-core kernels
+  void invalidate() { mop = mop3 = nullptr; }
 };
 
+// FP32-class filter products (the mixed form) of at least this many flops run as 3-slice
+// products on the tensor cores, smaller ones in FP32 on the CUDA cores.
+constexpr double OZ3_MIN_FLOPS = 1e8;
+
 // C (n x cols) = alpha Mop V + beta X + gamma Z, V n x cols (ld ldv).  With Mop32 (the mixed
-// form's filter, which needs only FP32 accuracy) the product runs in FP32 on the CUDA cores.
+// form's filter, which needs only FP32 accuracy) the product is FP32-class: 3-slice products of
+// Mop on the tensor cores, or FP32 on the CUDA cores with Mop32.
 int op_mv(EigOps& e, const double* Mop, const float* Mop32, const double* V, int64_t ldv,
           int cols, double alpha, double beta, const double* X, int64_t ldx, double gamma,
           const double* Z, int64_t ldz, double* C, int64_t ldc) {
   const int n = e.n;
+  if (Mop32 && 2.0 * n * (double)n * cols >= OZ3_MIN_FLOPS) {
+    if (e.mop3 != Mop) {
+      TK_TRY(oz_split_rows(Mop, n, n, n, nullptr, 0, 0, OZ_F32_SLICES, &e.msl3, e.s));
+      e.mop3 = Mop;
+    }
+    TK_TRY(oz_split_cols(V, ldv, n, cols, OZ_F32_SLICES, &e.b, e.s));
+    return oz_gemm_nt(e.msl3, e.b, false, alpha, beta, X, ldx, gamma, Z, ldz, C, ldc, e.status,
+                      e.s, "eig_mv_ozaki3");
+  }
   if (Mop32)
     return gemm_nn_f32a(n, cols, n, alpha, Mop32, n, V, ldv, beta, X, ldx, gamma, Z, ldz, C, ldc,
                         e.s);

@@ -10,7 +10,8 @@
 //     two, u = y 2^-e_i with |u| < 1/2, and cut into S integer slices of 8 bits,
 //     u = sum_s q_s 2^(-8(s+1)) + r with |q_s| <= 128 and |r| <= 2^-(8S+1) (each q_s exact in
 //     BF16).  S = 6 (48 bits) for the Grams and the HOOI projection, S = 7 (56 bits) for the
-//     eigensolver's products, whose rows can be dominated by a single entry;
+//     eigensolver's products, whose rows can be dominated by a single entry, and S = 3 (24
+//     bits, FP32-class) for the mixed form's filter products;
 //   * u_i . v_j = 2^-16 sum_d L_d 2^(-8d), with the level sums L_d = sum_{s+t=d} q_s(i).q_t(j)
 //     kept for d < S (S (S + 1) / 2 slice pairs).  For even S the first dropped level holds
 //     the square pair (S/2, S/2), whose products q_s(k)^2 on a Gram's diagonal do not average
@@ -30,8 +31,9 @@
 // Layout: one CTA computes a 128 x 64 tile (rows of A = tile ti of 128 rows, rows of B^T =
 // tile tj of 64 rows; for a symmetric product only tj <= 2 ti + 1, the lower triangle) over a
 // range of K stages of 32 columns.  Warp 0 streams all S slices of A (128 x 32) and B (64 x 32)
-// of a stage with two 3-D TMA loads (64-byte swizzle) through a 3-stage (S = 6) or 2-stage
-// (S = 7) ring; warp 1 issues the 44 or 56 MMAs of a stage (M = 128, N = 64, K = 16,
+// of a stage with two 3-D TMA loads (64-byte swizzle) through a 6-stage (S = 3), 3-stage (S = 6)
+// or 2-stage (S = 7) ring; warp 1 issues the 12, 44 or 56 MMAs of a stage (M = 128, N = 64,
+// K = 16,
 // kind::f16); warps 2-9 read the level accumulators out.  Every wait is bounded: on a timeout
 // the kernel records DEV_TIMEOUT, drains and returns.
 #include <cudaTypedefs.h>
@@ -56,11 +58,11 @@ constexpr uint32_t IDESC = tc::idesc_bf16(TM, TN);
 // S <= 7: 7 levels x 64 columns fit in tensor memory, and 8 S bits fit the 64-bit split.
 template <int S>
 struct Geo {
-  static_assert(S >= 5 && S <= 7, "5 to 7 slices per operand");
+  static_assert(S == 3 || (S >= 5 && S <= 7), "3 or 5 to 7 slices per operand");
   static constexpr int A_BYTES = S * TM * KS * 2;
   static constexpr int B_BYTES = S * TN * KS * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int NSTAGE = S <= 6 ? 3 : 2;
+  static constexpr int NSTAGE = S <= 3 ? 6 : S <= 6 ? 3 : 2;
   static constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 512;
   // Levels: d < S, plus for even S a level S holding the one pair (S/2, S/2) (see the file
   // comment); the lowest level is 6 for S = 6 and S = 7.
@@ -556,7 +558,7 @@ int make_slice_map(CUtensorMap* m, const OzSlices& S, int box_rows) {
 }
 
 int reserve(OzSlices* out, int rows, int64_t ldK, int nslice, cudaStream_t s) {
-  if (nslice != 6 && nslice != 7) return TUCKER_EINVAL;
+  if (nslice != 3 && nslice != 6 && nslice != 7) return TUCKER_EINVAL;
   out->nslice = nslice;
   out->rows = rows;
   out->rows_pad = ceil_div(rows, TM) * TM;
@@ -585,7 +587,8 @@ int oz_split_rows(const double* A, int64_t lda, int rows, int64_t K1, const doub
   TK_LAUNCH();
   if (out->ldK == 0) return TUCKER_OK;   // no columns: nothing to cut
   const int64_t quads = (int64_t)out->rows_pad * (out->ldK / 4);
-  auto kern = nslice == 7 ? oz_split_rows_kernel<7> : oz_split_rows_kernel<6>;
+  auto kern = nslice == 7 ? oz_split_rows_kernel<7>
+              : nslice == 6 ? oz_split_rows_kernel<6> : oz_split_rows_kernel<3>;
   kern<<<ceil_div(quads, 256), 256, 0, s>>>(rows, out->rows_pad, A, lda, K1, K1p, A2, lda2, K2,
                                             out->ldK, out->ex.as<int>(),
                                             out->Q.as<__nv_bfloat16>());
@@ -608,7 +611,8 @@ int oz_split_cols(const double* B, int64_t ldb, int64_t K, int cols, int nslice,
   oz_fix_zero_cols<<<ceil_div(cols, 256), 256, 0, s>>>(cols, out->ex.as<int>());
   TK_LAUNCH();
   if (out->ldK == 0) return TUCKER_OK;   // no rows of B: nothing to cut
-  auto kern = nslice == 7 ? oz_split_cols_kernel<7> : oz_split_cols_kernel<6>;
+  auto kern = nslice == 7 ? oz_split_cols_kernel<7>
+              : nslice == 6 ? oz_split_cols_kernel<6> : oz_split_cols_kernel<3>;
   kern<<<dim3(out->rows_pad / 32, (unsigned)(out->ldK / 32)), dim3(32, 8), 0, s>>>(
       B, ldb, K, cols, out->rows_pad, out->ldK, out->ex.as<int>(), out->Q.as<__nv_bfloat16>());
   TK_LAUNCH();
@@ -684,8 +688,10 @@ int oz_gemm_nt(const OzSlices& A, const OzSlices& B, bool sym, double alpha, dou
                      16.0 * TM * TN * (double)njobs);
     if (S == 7)
       TK_TRY(launch_products<7>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
-    else
+    else if (S == 6)
       TK_TRY(launch_products<6>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
+    else
+      TK_TRY(launch_products<3>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
   }
   oz_reduce<<<ceil_div((int64_t)m * n, 256), 256, 0, s>>>(part.as<long long>(), g, S, m, n,
                                                            A.ex.as<int>(), B.ex.as<int>(), alpha,

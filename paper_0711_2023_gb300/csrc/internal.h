@@ -125,7 +125,8 @@ struct OzSlices {
   int rows = 0, rows_pad = 0;
   int64_t ldK = 0;
 };
-constexpr int OZ_GRAM_SLICES = 6, OZ_GEMM_SLICES = 7;
+// nslice = 3 keeps 24 bits (an FP32-class product, for the mixed form's filter).
+constexpr int OZ_GRAM_SLICES = 6, OZ_GEMM_SLICES = 7, OZ_F32_SLICES = 3;
 int64_t oz_ldk(int64_t K);
 // Slices of the rows of [A | A2] (A: rows x K1, ld lda; A2 optional: rows x K2, ld lda2).
 int oz_split_rows(const double* A, int64_t lda, int rows, int64_t K1, const double* A2,
