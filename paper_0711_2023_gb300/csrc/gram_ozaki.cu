@@ -32,9 +32,9 @@
 // tile tj of 64 rows; for a symmetric product only tj <= 2 ti + 1, the lower triangle) over a
 // range of K stages of 32 columns.  Warp 0 streams all S slices of A (128 x 32) and B (64 x 32)
 // of a stage with two 3-D TMA loads (64-byte swizzle) through a 6-stage (S = 3), 3-stage (S = 6)
-// or 2-stage (S = 7) ring; warp 1 issues the 12, 44 or 56 MMAs of a stage (M = 128, N = 64,
-// K = 16,
-// kind::f16); warps 2-9 read the level accumulators out.  Every wait is bounded: on a timeout
+// or 2-stage (S = 7) ring; warps 1 and 2 issue the 12, 44 or 56 MMAs of a stage (M = 128,
+// N = 64, K = 16, kind::f16), each for its own levels; warps 3-10 read the level accumulators
+// out.  Every wait is bounded: on a timeout
 // the kernel records DEV_TIMEOUT, drains and returns.
 #include <cudaTypedefs.h>
 
@@ -50,7 +50,11 @@ namespace {
 
 constexpr int BETA = 8;                              // bits per slice
 constexpr int TM = 128, TN = 64, KS = 32;
-constexpr int NTHREADS = 320;                        // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+// Issuing a tcgen05.mma costs its thread about 100 cycles, three times what an M = 128, N = 64
+// MMA takes on the tensor pipe, so the levels are split between NMMA issuing warps (balanced by
+// slice pairs), each committing its own MMAs.
+constexpr int NMMA = 2;
+constexpr int NTHREADS = 32 * (1 + NMMA + 8);   // warp 0 TMA, warps 1..NMMA MMA, then 8 epilogue
 constexpr uint32_t IDESC = tc::idesc_bf16(TM, TN);
 
 // Ring geometry for S slices per operand (S levels, S (S + 1) / 2 slice pairs): one stage holds
@@ -84,6 +88,15 @@ __host__ __device__ constexpr int level_chunk(int d) {
 }
 __host__ __device__ constexpr int level_residue(int d) {
   return d == 0 ? 0 : d == 1 ? 8 : d == 2 ? 2 : d == 3 ? 6 : d == 4 ? 1 : d == 5 ? 3 : 0;
+}
+// Issuing warp (0 .. NMMA - 1) of level d: pair counts per level are 1, 2, ..., S (and 1 for
+// the square-pair level of an even S); the two halves hold 11 + 11 (S = 6), 14 + 14 (S = 7) and
+// 3 + 3 (S = 3) pairs.
+template <int S>
+__host__ __device__ constexpr int level_owner(int d) {
+  return S == 6 ? ((d == 4 || d == 5) ? 1 : 0)
+       : S == 7 ? ((d == 0 || d == 5 || d == 6) ? 0 : 1)
+                : (d == 2 ? 1 : 0);
 }
 // Stages per K split or per batched job: at most 2^19 (2^24 columns), so that the integer
 // sums of a job, |hi| <= K 2^14 (2^24 + 2^17 + 3 2^8 + 4), stay below 2^63.
@@ -174,13 +187,13 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&empty[s], NMMA);   // one commit per issuing warp
     }
     for (int d = 0; d < NL; ++d) {
       tc::mbar_init(&acc_full[d], 1);
       tc::mbar_init(&acc_free[d], 8);   // one arrival per epilogue warp
     }
-    tc::mbar_init(done, 1);
+    tc::mbar_init(done, NMMA);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -208,7 +221,8 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
     if (*abort_flag)
       for (int j = issued > STAGES ? issued - STAGES : 0; j < issued; ++j)
         tc::mbar_drain(&full[j % STAGES], (j / STAGES) & 1);
-  } else if (warp == 1 && lane == 0) {
+  } else if (warp >= 1 && warp <= NMMA && lane == 0) {
+    const int mi = warp - 1;   // this thread issues the levels d with level_owner<S>(d) == mi
     // ---- MMA issuer ----------------------------------------------------------------------------
     uint32_t free_phase = 0;   // bit d: parity of the next acc_free[d] phase to wait for
     bool ok = true;
@@ -230,6 +244,7 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
       for (int pass = 0; pass < 2; ++pass) {
 #pragma unroll
         for (int d = 0; d < NL; ++d) {
+          if (level_owner<S>(d) != mi) continue;
           const bool rs = (rm >> d) & 1u;
           if (pass == 0 ? rs : !rs) continue;
           if (rs) {
@@ -262,13 +277,14 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
       tc::mma_commit(&empty[s]);
       const bool last = j + 1 == job.ns;
       for (int d = 0; d < NL; ++d)
-        if (last || restarts(d, j + 1)) tc::mma_commit(&acc_full[d]);
+        if (level_owner<S>(d) == mi && (last || restarts(d, j + 1)))
+          tc::mma_commit(&acc_full[d]);
     }
     tc::mma_commit(done);   // arrives once every MMA issued above has completed
-  } else if (warp >= 2) {
+  } else if (warp > NMMA) {
     // ---- epilogue: level readouts into exact 64-bit integer sums -----------------------------
     const int q = warp & 3;              // TMEM lane quarter this warp may access
-    const int h = (warp - 2) >> 2;       // column half of the 64-column level accumulator
+    const int h = (warp - NMMA - 1) >> 2;   // column half of the 64-column level accumulator
     long long hi[32], lo[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0;
