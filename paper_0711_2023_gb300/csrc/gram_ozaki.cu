@@ -28,7 +28,15 @@
 //   * a reduction kernel adds the K splits' integer partials, scales them back to FP64 and
 //     applies the epilogue alpha C + beta X + gamma Z.
 //
-// Layout: one CTA computes a 128 x 64 tile (rows of A = tile ti of 128 rows, rows of B^T =
+// Two kernels.  A tcgen05.mma instruction costs about the same for N = 64 and N = 128 (its
+// issue, not the tensor pipe, sets the rate), so the long symmetric Grams use 128 x 128 tiles
+// (wk::): tensor memory then holds only four level accumulators of 128 columns, and the levels
+// run in two passes over the job's K range (levels 0-3 from slices 0-3, then the lower levels
+// from all slices; 16 epilogue warps, 32 columns each).  The other products (the eigensolver's,
+// whose B has ~150 columns, and the per-slice HOOI products with few stages each) use 128 x 64
+// tiles in one pass (nk::), described below.
+//
+// Layout (nk::): one CTA computes a 128 x 64 tile (rows of A = tile ti of 128 rows, rows of B^T =
 // tile tj of 64 rows; for a symmetric product only tj <= 2 ti + 1, the lower triangle) over a
 // range of K stages of 32 columns.  Warp 0 streams all S slices of A (128 x 32) and B (64 x 32)
 // of a stage with two 3-D TMA loads (64-byte swizzle) through a 6-stage (S = 3), 3-stage (S = 6)
@@ -49,11 +57,77 @@ namespace tk {
 namespace {
 
 constexpr int BETA = 8;                              // bits per slice
-constexpr int TM = 128, TN = 64, KS = 32;
-// Issuing a tcgen05.mma costs its thread about 100 cycles, three times what an M = 128, N = 64
-// MMA takes on the tensor pipe, so the levels are split between NMMA issuing warps (balanced by
-// slice pairs), each committing its own MMAs.
+constexpr int TM = 128, KS = 32;
+// Issuing a tcgen05.mma costs its thread about 100 cycles -- three times what an M = 128, N = 64
+// MMA takes on the tensor pipe, and about the same for N = 128 -- so the levels are split between
+// NMMA issuing warps (balanced by slice pairs), each committing its own MMAs, and long products
+// use N = 128.
 constexpr int NMMA = 2;
+// Lowest level kept for nslice slices (the lo sum is scaled by 2^-8 LT).
+__host__ __device__ constexpr int oz_lowest_level(int nslice) {
+  return nslice % 2 == 0 ? nslice : nslice - 1;
+}
+// Stages per K split or per batched job: at most 2^19 (2^24 columns), so that the integer
+// sums of a job, |hi| <= K 2^14 (2^24 + 2^17 + 3 2^8 + 4), stay below 2^63.
+constexpr int MAX_JOB_STAGES = 1 << 19;
+
+// Grid geometry: CTA b computes tile pair b % npairs over K split b / npairs.  Tiles are
+// 128 x tn (tn = 64 or 128).  Tile pairs are numbered row by row: (ti, tj) -> ti * ntj + tj, or
+// for a symmetric product (the lower triangle: tj <= 2 ti + 1 when tn = 64, every row but
+// possibly the last holding 2 ti + 2 pairs; tj <= ti when tn = 128) ti (ti + 1) + tj or
+// ti (ti + 1) / 2 + tj.
+struct Grid {
+  int ntj, npairs, nsplit, nst;
+  int sym;
+  int tn;
+  // Batched products (one product per slice, each over its own stage range): CTA b computes
+  // tile pair b % npairs of slice b / npairs over stages [stage_start[i], stage_start[i + 1]).
+  const int* stage_start;
+};
+
+struct Job {
+  int ti, tj;   // 128-row tile of A, tn-row tile of B^T
+  int s0, ns;   // first K stage and number of stages
+};
+
+__host__ __device__ inline void pair_tiles(const Grid& g, int p, int* ti, int* tj) {
+  if (!g.sym) {
+    *ti = p / g.ntj;
+    *tj = p % g.ntj;
+    return;
+  }
+  const int f = g.tn == 64 ? 2 : 1;   // row t starts at f t (t + 1) / 2
+  int t = (int)((sqrt(8.0 / f * (double)p + 1.0) - 1.0) * 0.5);
+  while (f * t * (t + 1) / 2 > p) --t;
+  while (f * (t + 1) * (t + 2) / 2 <= p) ++t;
+  *ti = t;
+  *tj = p - f * t * (t + 1) / 2;
+}
+
+__host__ __device__ inline int pair_index(const Grid& g, int ti, int tj) {
+  return g.sym ? (g.tn == 64 ? ti * (ti + 1) : ti * (ti + 1) / 2) + tj : ti * g.ntj + tj;
+}
+
+__device__ inline Job job_of(const Grid& g, int b) {
+  Job j;
+  if (g.stage_start) {
+    const int i = b / g.npairs, p = b % g.npairs;
+    j.ti = p / g.ntj;
+    j.tj = p % g.ntj;
+    j.s0 = g.stage_start[i];
+    j.ns = g.stage_start[i + 1] - j.s0;
+    return j;
+  }
+  const int z = b / g.npairs, p = b % g.npairs;
+  pair_tiles(g, p, &j.ti, &j.tj);
+  j.s0 = (int)((int64_t)g.nst * z / g.nsplit);
+  j.ns = (int)((int64_t)g.nst * (z + 1) / g.nsplit) - j.s0;
+  return j;
+}
+
+// ---- 128 x 64 tiles, one pass: every level has a 64-column accumulator in tensor memory ------
+namespace nk {
+constexpr int TN = 64;
 constexpr int NTHREADS = 32 * (1 + NMMA + 8);   // warp 0 TMA, warps 1..NMMA MMA, then 8 epilogue
 constexpr uint32_t IDESC = tc::idesc_bf16(TM, TN);
 
@@ -73,10 +147,6 @@ struct Geo {
   static constexpr int NL = S % 2 == 0 ? S + 1 : S;
   static constexpr int PAIRS = S * (S + 1) / 2 + (S % 2 == 0 ? 1 : 0);
 };
-// Lowest level kept for nslice slices (the lo sum is scaled by 2^-8 LT).
-__host__ __device__ constexpr int oz_lowest_level(int nslice) {
-  return nslice % 2 == 0 ? nslice : nslice - 1;
-}
 
 // Readout schedule of level d: its accumulator restarts at local stage j > 0 when
 // j % CHUNK[d] == RESIDUE[d].  A chunk spans at most CHUNK[d] stages of 32 columns, and
@@ -98,9 +168,6 @@ __host__ __device__ constexpr int level_owner(int d) {
        : S == 7 ? ((d == 0 || d == 5 || d == 6) ? 0 : 1)
                 : (d == 2 ? 1 : 0);
 }
-// Stages per K split or per batched job: at most 2^19 (2^24 columns), so that the integer
-// sums of a job, |hi| <= K 2^14 (2^24 + 2^17 + 3 2^8 + 4), stay below 2^63.
-constexpr int MAX_JOB_STAGES = 1 << 19;
 __device__ __forceinline__ bool restarts(int d, int j) {
   return j > 0 && j % level_chunk(d) == level_residue(d);
 }
@@ -114,56 +181,6 @@ __device__ __forceinline__ uint32_t restart_mask(int j) {
       if ((j & (level_chunk(d) - 1)) == level_residue(d)) m |= 1u << d;
   }
   return m;
-}
-
-// Grid geometry: CTA b computes tile pair b % npairs over K split b / npairs.  Tile pairs are
-// numbered row by row: (ti, tj) -> ti * ntj + tj, or for a symmetric product (tj <= 2 ti + 1,
-// every row but possibly the last has 2 ti + 2 pairs) ti (ti + 1) + tj.
-struct Grid {
-  int ntj, npairs, nsplit, nst;
-  int sym;
-  // Batched products (one product per slice, each over its own stage range): CTA b computes
-  // tile pair b % npairs of slice b / npairs over stages [stage_start[i], stage_start[i + 1]).
-  const int* stage_start;
-};
-
-struct Job {
-  int ti, tj;   // 128-row tile of A, 64-row tile of B^T
-  int s0, ns;   // first K stage and number of stages
-};
-
-__host__ __device__ inline void pair_tiles(const Grid& g, int p, int* ti, int* tj) {
-  if (!g.sym) {
-    *ti = p / g.ntj;
-    *tj = p % g.ntj;
-    return;
-  }
-  int t = (int)((sqrt(4.0 * (double)p + 1.0) - 1.0) * 0.5);
-  while (t * (t + 1) > p) --t;
-  while ((t + 1) * (t + 2) <= p) ++t;
-  *ti = t;
-  *tj = p - t * (t + 1);
-}
-
-__host__ __device__ inline int pair_index(const Grid& g, int ti, int tj) {
-  return g.sym ? ti * (ti + 1) + tj : ti * g.ntj + tj;
-}
-
-__device__ inline Job job_of(const Grid& g, int b) {
-  Job j;
-  if (g.stage_start) {
-    const int i = b / g.npairs, p = b % g.npairs;
-    j.ti = p / g.ntj;
-    j.tj = p % g.ntj;
-    j.s0 = g.stage_start[i];
-    j.ns = g.stage_start[i + 1] - j.s0;
-    return j;
-  }
-  const int z = b / g.npairs, p = b % g.npairs;
-  pair_tiles(g, p, &j.ti, &j.tj);
-  j.s0 = (int)((int64_t)g.nst * z / g.nsplit);
-  j.ns = (int)((int64_t)g.nst * (z + 1) / g.nsplit) - j.s0;
-  return j;
 }
 
 template <int S>
@@ -342,6 +359,315 @@ gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
   }
 }
 
+}  // namespace nk
+
+// ---- 128 x 128 tiles, two passes over K (the long Grams): four 128-column accumulators ------
+namespace wk {
+constexpr int TN = 128;
+// 16 epilogue warps: four per TMEM lane quarter, each reading 32 columns of a 128-column slot
+// (32 int64 sums per thread).
+constexpr int NEPI = 16;
+constexpr int NTHREADS = 32 * (1 + NMMA + NEPI);   // warp 0 TMA, warps 1..NMMA MMA, epilogue
+constexpr uint32_t IDESC = tc::idesc_bf16(TM, TN);
+constexpr int SLOT_COLS = TN;                    // one level accumulator: 128 FP32 columns
+constexpr int RING_BYTES = 224 * 1024;
+
+// Tensor memory holds four 128-column accumulators, so the levels run in two passes over the
+// job's K range: pass 0 the levels d <= 3 (slices 0..3; levels 0..2 and slices 0..2 when S = 3),
+// pass 1 the lower levels (all S slices).  A stage of a pass holds its slices of A and of B
+// (8 KB each per slice); the ring of each pass fills RING_BYTES.
+template <int S>
+struct Geo {
+  static_assert(S == 3 || (S >= 5 && S <= 7), "3 or 5 to 7 slices per operand");
+  // Levels: d < S, plus for even S a level S holding the one pair (S/2, S/2) (see the file
+  // comment); the lowest level is 6 for S = 6 and S = 7.
+  static constexpr int NL = S % 2 == 0 ? S + 1 : S;
+  static constexpr int PAIRS = S * (S + 1) / 2 + (S % 2 == 0 ? 1 : 0);
+  static constexpr int NL0 = NL < 4 ? NL : 4;    // levels of pass 0
+  static constexpr int NL1 = NL - NL0;           // levels of pass 1
+  static constexpr int SL0 = NL0;                // slices of pass 0
+  static constexpr int SL1 = S;                  // slices of pass 1
+  static constexpr int SLICE_BYTES = TM * KS * 2;   // = TN * KS * 2
+  static constexpr int STAGE0 = 2 * SL0 * SLICE_BYTES;
+  static constexpr int STAGE1 = 2 * SL1 * SLICE_BYTES;
+  static constexpr int NST0 = RING_BYTES / STAGE0 < 4 ? RING_BYTES / STAGE0 : 4;
+  static constexpr int NST1 = RING_BYTES / STAGE1 < 4 ? RING_BYTES / STAGE1 : 4;
+  static_assert(NST0 >= 2 && (NL1 == 0 || NST1 >= 2), "ring too small");
+  static constexpr int SMEM_BYTES = RING_BYTES + 1024 + 512;
+};
+
+// Readout schedule of level d: its accumulator restarts at local stage j > 0 of its pass when
+// j % CHUNK[d] == RESIDUE[d].  A chunk spans at most CHUNK[d] stages of 32 columns, and
+// pairs(d) CHUNK[d] <= 32, so a chunk sums at most 32 x 32 products of magnitude <= 2^14:
+// |L| <= 2^24, every partial sum is an integer that FP32 holds exactly (pairs(d) = d + 1, and 1
+// for the square-pair level S of an even S).  The residues spread the restarts of a pass.
+template <int S>
+__host__ __device__ constexpr int level_chunk(int d) {
+  return d == 0 ? 32 : d == 1 ? 16 : d <= 3 ? 8 : d <= 5 ? 4 : (S % 2 == 0 ? 32 : 4);
+}
+template <int S>
+__host__ __device__ constexpr int level_residue(int d) {
+  return d == 0 ? 8 : d == 1 ? 4 : d == 2 ? 2 : d == 3 ? 6 : d == 4 ? 1 : d == 5 ? 3 : 2;
+}
+// Issuing warp (0 .. NMMA - 1) of level d, balancing slice pairs within each pass: pass 0 puts
+// levels {0, 3} (5 pairs) and {1, 2} (5) apart; pass 1 {4, S} (6) and {5} (6) for S = 6, {4, 5}
+// (11) and {6} (7) for S = 7; S = 3 has {0, 1} (3) and {2} (3).
+template <int S>
+__host__ __device__ constexpr int level_owner(int d) {
+  return S == 3 ? (d == 2 ? 1 : 0)
+       : d <= 3 ? ((d == 0 || d == 3) ? 0 : 1)
+       : S == 6 ? (d == 5 ? 1 : 0)
+                : (d == 6 ? 1 : 0);
+}
+template <int S>
+__device__ __forceinline__ bool restarts(int d, int j) {
+  return j > 0 && (j & (level_chunk<S>(d) - 1)) == level_residue<S>(d);
+}
+
+// Barriers of one pass: ring full/empty, per-slot chunk complete / read out.
+struct PassBars {
+  uint64_t* full;
+  uint64_t* empty;
+  uint64_t* acc_full;
+  uint64_t* acc_free;
+};
+
+template <int S>
+__global__ void __launch_bounds__(NTHREADS, 1)
+gram_ozaki_kernel(const __grid_constant__ CUtensorMap mapA0,
+                  const __grid_constant__ CUtensorMap mapB0,
+                  const __grid_constant__ CUtensorMap mapA1,
+                  const __grid_constant__ CUtensorMap mapB1, const Grid grid,
+                  long long* __restrict__ partial, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  using G = Geo<S>;
+  constexpr int NL = G::NL, LT = NL - 1;
+  uint64_t* bars = (uint64_t*)(smem + RING_BYTES);
+  PassBars pb[2];
+  pb[0].full = bars;                       // [NST0]
+  pb[0].empty = pb[0].full + G::NST0;      // [NST0]
+  pb[1].full = pb[0].empty + G::NST0;      // [NST1]
+  pb[1].empty = pb[1].full + G::NST1;      // [NST1]
+  pb[0].acc_full = pb[1].empty + G::NST1;  // [4] slots of pass 0
+  pb[0].acc_free = pb[0].acc_full + 4;
+  pb[1].acc_full = pb[0].acc_free + 4;     // [4] slots of pass 1
+  pb[1].acc_free = pb[1].acc_full + 4;
+  uint64_t* pass_free = pb[1].acc_free + 4;   // the epilogue has read pass 0 out
+  uint64_t* done = pass_free + 1;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Job job = job_of(grid, blockIdx.x);
+
+  if (threadIdx.x == 0) {
+    for (int p = 0; p < 2; ++p) {
+      const int nst = p == 0 ? G::NST0 : G::NST1;
+      for (int s = 0; s < nst; ++s) {
+        tc::mbar_init(&pb[p].full[s], 1);
+        tc::mbar_init(&pb[p].empty[s], NMMA);   // one commit per issuing warp
+      }
+      for (int t = 0; t < 4; ++t) {
+        tc::mbar_init(&pb[p].acc_full[t], 1);
+        tc::mbar_init(&pb[p].acc_free[t], NEPI);   // one arrival per epilogue warp
+      }
+    }
+    tc::mbar_init(pass_free, NEPI);
+    tc::mbar_init(done, NMMA);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: the pass's slices of A and B for one K stage per ring slot -----------
+    bool ok = true;
+    for (int p = 0; p < 2 && ok; ++p) {
+      if (p == 1 && G::NL1 == 0) break;
+      const int nst = p == 0 ? G::NST0 : G::NST1;
+      const int stage_bytes = p == 0 ? G::STAGE0 : G::STAGE1;
+      const int a_bytes = stage_bytes / 2;
+      const CUtensorMap* mA = p == 0 ? &mapA0 : &mapA1;
+      const CUtensorMap* mB = p == 0 ? &mapB0 : &mapB1;
+      int issued = 0;
+      for (int j = 0; j < job.ns; ++j) {
+        const int s = j % nst;
+        if (j >= nst &&
+            !tc::mbar_wait(&pb[p].empty[s], ((j / nst) - 1) & 1, status, abort_flag)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + s * stage_bytes;
+        tc::mbar_expect_tx(&pb[p].full[s], stage_bytes);
+        const int kx = (job.s0 + j) * KS;
+        tc::tma_load_3d(st, mA, &pb[p].full[s], kx, job.ti * TM, 0);
+        tc::tma_load_3d(st + a_bytes, mB, &pb[p].full[s], kx, job.tj * TN, 0);
+        ++issued;
+      }
+      if (!ok) {
+        for (int j = issued > nst ? issued - nst : 0; j < issued; ++j)
+          tc::mbar_drain(&pb[p].full[j % nst], (j / nst) & 1);
+        break;
+      }
+      // The ring is reused by the next pass with another layout: wait until the MMAs have read
+      // every stage of this one.
+      for (int j = job.ns > nst ? job.ns - nst : 0; j < job.ns; ++j)
+        if (!tc::mbar_wait(&pb[p].empty[j % nst], (j / nst) & 1, status, abort_flag)) {
+          ok = false;
+          break;
+        }
+    }
+  } else if (warp >= 1 && warp <= NMMA && lane == 0) {
+    const int mi = warp - 1;   // this thread issues the levels d with level_owner<S>(d) == mi
+    // ---- MMA issuers ---------------------------------------------------------------------------
+    bool ok = true;
+    for (int p = 0; p < 2 && ok; ++p) {
+      if (p == 1 && G::NL1 == 0) break;
+      const int nst = p == 0 ? G::NST0 : G::NST1;
+      const int stage_bytes = p == 0 ? G::STAGE0 : G::STAGE1;
+      const int d0 = p == 0 ? 0 : G::NL0, d1 = p == 0 ? G::NL0 : NL;   // levels [d0, d1)
+      if (p == 1) {
+        // pass 1 writes the slots pass 0's last chunks are read from
+        if (!tc::mbar_wait(pass_free, 0, status, abort_flag)) break;
+        tc::fence_after();
+      }
+      uint32_t free_phase = 0;   // bit t: parity of the next acc_free[t] phase to wait for
+      for (int j = 0; j < job.ns && ok; ++j) {
+        const int s = j % nst;
+        if (!tc::mbar_wait(&pb[p].full[s], (j / nst) & 1, status, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        const uint8_t* st = smem + s * stage_bytes;
+        // Slice q of A (B) starts q * 8 KB after the first: descriptor address field + q * 512
+        // (the ring lies below 256 KB, so the 14-bit field does not overflow).
+        const uint64_t da0 = tc::sw_desc(st, 64), db0 = tc::sw_desc(st + stage_bytes / 2, 64);
+        constexpr uint64_t DS = G::SLICE_BYTES >> 4;
+        // Levels that keep accumulating first, then the restarting ones (their slot must first
+        // have been read out).
+#pragma unroll
+        for (int ph = 0; ph < 2; ++ph) {
+#pragma unroll
+          for (int d = 0; d < NL; ++d) {
+            if (d < d0 || d >= d1 || level_owner<S>(d) != mi) continue;
+            const bool rs = restarts<S>(d, j);
+            if (ph == 0 ? rs : !rs) continue;
+            const int t = d - d0;
+            if (rs) {
+              if (!tc::mbar_wait(&pb[p].acc_free[t], (free_phase >> t) & 1u, status,
+                                 abort_flag)) {
+                ok = false;
+                break;
+              }
+              free_phase ^= 1u << t;
+              tc::fence_after();
+            }
+            const uint32_t dt = tmem + (uint32_t)(t * SLOT_COLS);
+            const uint32_t acc0 = (j == 0 || rs) ? 0u : 1u;
+#pragma unroll
+            for (int kk = 0; kk < KS / 16; ++kk) {
+              const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
+              if (d < S) {
+#pragma unroll
+                for (int q = 0; q <= d; ++q)
+                  tc::mma_bf16<IDESC>(dt, da0 + (q * DS + off), db0 + ((d - q) * DS + off),
+                                      (kk == 0 && q == 0) ? acc0 : 1u);
+              } else {   // level S: the pair (S/2, S/2) only
+                tc::mma_bf16<IDESC>(dt, da0 + ((S / 2) * DS + off), db0 + ((S / 2) * DS + off),
+                                    kk == 0 ? acc0 : 1u);
+              }
+            }
+          }
+          if (!ok) break;
+        }
+        if (!ok) break;
+        tc::mma_commit(&pb[p].empty[s]);
+        const bool last = j + 1 == job.ns;
+#pragma unroll
+        for (int d = 0; d < NL; ++d)
+          if (d >= d0 && d < d1 && level_owner<S>(d) == mi && (last || restarts<S>(d, j + 1)))
+            tc::mma_commit(&pb[p].acc_full[d - d0]);
+      }
+    }
+    tc::mma_commit(done);   // arrives once every MMA issued above has completed
+  } else if (warp > NMMA) {
+    // ---- epilogue: level readouts into exact 64-bit integer sums, one pass at a time --------
+    const int q = warp & 3;                   // TMEM lane quarter this warp may access
+    const int c4 = (warp - NMMA - 1) >> 2;    // 32-column quarter of a 128-column slot
+    const int row = q * 32 + lane;
+    long long* out = partial + (int64_t)blockIdx.x * 2 * TM * TN + (int64_t)row * TN + c4 * 32;
+    bool ok = true;
+    for (int p = 0; p < 2; ++p) {
+      long long acc[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[i] = 0;
+      const int d0 = p == 0 ? 0 : G::NL0, d1 = p == 0 ? G::NL0 : NL;
+      uint32_t full_phase = 0;   // bit t: parity of the next acc_full[t] phase to wait for
+      auto readout = [&](int d) {
+        if (!ok) return;
+        const int t = d - d0;
+        if (!tc::mbar_wait(&pb[p].acc_full[t], (full_phase >> t) & 1u, status, abort_flag)) {
+          ok = false;
+          return;
+        }
+        full_phase ^= 1u << t;
+        tc::fence_after();
+        const uint32_t ta =
+            tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * SLOT_COLS + c4 * 32);
+        // |L| <= 2^24 and integral: the conversion is exact.
+        const int sh = d <= 3 ? BETA * (3 - d) : BETA * (LT - d);
+        uint32_t r[16];
+        tc::tmem_ld16_raw(ta, r);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] += (long long)__float2int_rn(__uint_as_float(r[i])) << sh;
+        tc::tmem_ld16_raw(ta + 16, r);
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&pb[p].acc_free[t]);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          acc[16 + i] += (long long)__float2int_rn(__uint_as_float(r[i])) << sh;
+      };
+      if (!(p == 1 && G::NL1 == 0)) {
+        for (int j = 1; j < job.ns && ok; ++j)
+          for (int d = d0; d < d1; ++d)
+            if (restarts<S>(d, j)) readout(d);
+        if (job.ns > 0)
+          for (int d = d0; d < d1; ++d) readout(d);
+      }
+      if (p == 0) {
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(pass_free);
+      }
+      // pass 0 gives hi = sum_{d<=3} L_d 2^(8(3-d)), pass 1 lo = sum_{d>=4} L_d 2^(8(6-d))
+      if (__all_sync(0xffffffffu, ok && !*abort_flag)) {
+        long long* o = out + (p == 0 ? 0 : TM * TN);
+#pragma unroll
+        for (int i = 0; i < 32; i += 2)
+          *reinterpret_cast<longlong2*>(o + i) = make_longlong2(acc[i], acc[i + 1]);
+      }
+    }
+  }
+  __syncwarp();
+  // Nobody frees tensor memory while MMAs may still be in flight.
+  if (!tc::mbar_wait(done, 0, status, abort_flag)) tc::mbar_drain(done, 0);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, 512);
+  }
+}
+
+}  // namespace wk
+
 // The splitting runs in integer arithmetic on the FP64 bit patterns (this part's FP64 pipe
 // is far too slow for it).  A row's scale exponent e satisfies |y 2^-e| < 1/2 for every y in
 // the row: e = frexp exponent of max |y| + 1, computed from the largest |y| bit pattern (for
@@ -512,13 +838,14 @@ __global__ void oz_reduce(const long long* __restrict__ partial, const Grid g, i
   if (t >= (int64_t)m * n) return;
   const int r = (int)(t / n), c = (int)(t % n);
   if (g.sym && c > r) return;
-  const int ti = r / TM, tj = c / TN;
+  const int tn = g.tn;
+  const int ti = r / TM, tj = c / tn;
   const int p = pair_index(g, ti, tj);
-  const int rr = r - ti * TM, cc = c - tj * TN;
+  const int rr = r - ti * TM, cc = c - tj * tn;
   long long hh = 0, hl = 0, lh = 0, ll = 0;
   for (int z = 0; z < g.nsplit; ++z) {
-    const long long* P = partial + ((int64_t)z * g.npairs + p) * 2 * TM * TN;
-    const long long a = P[rr * TN + cc], b = P[TM * TN + rr * TN + cc];
+    const long long* P = partial + ((int64_t)z * g.npairs + p) * 2 * TM * tn;
+    const long long a = P[rr * tn + cc], b = P[TM * tn + rr * tn + cc];
     hh += a >> 32;
     hl += a & 0xFFFFFFFFll;
     lh += b >> 32;
@@ -552,8 +879,9 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// 3-D map over the slice planes: (k, row, slice), box (32, box_rows, 7), 64-byte swizzle.
-int make_slice_map(CUtensorMap* m, const OzSlices& S, int box_rows) {
+// 3-D map over the slice planes: (k, row, slice), box (32, box_rows, box_slices) -- the first
+// box_slices slices of a stage -- with 64-byte swizzle.
+int make_slice_map(CUtensorMap* m, const OzSlices& S, int box_rows, int box_slices) {
   auto enc = get_encode();
   if (!enc) {
     set_error_detail("cuTensorMapEncodeTiled is not available from the driver");
@@ -561,7 +889,7 @@ int make_slice_map(CUtensorMap* m, const OzSlices& S, int box_rows) {
   }
   cuuint64_t dims[3] = {(cuuint64_t)S.ldK, (cuuint64_t)S.rows_pad, (cuuint64_t)S.nslice};
   cuuint64_t strides[2] = {(cuuint64_t)S.ldK * 2, (cuuint64_t)S.rows_pad * (cuuint64_t)S.ldK * 2};
-  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)box_rows, (cuuint32_t)S.nslice};
+  cuuint32_t box[3] = {(cuuint32_t)KS, (cuuint32_t)box_rows, (cuuint32_t)box_slices};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S.Q.p, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -637,14 +965,36 @@ int oz_split_cols(const double* B, int64_t ldb, int64_t K, int cols, int nslice,
 
 namespace {
 
+// The tensor maps and the products: 128 x 64 tiles in one pass (tensor maps of all S slices), or
+// 128 x 128 tiles in two passes (pass 0 loads the first wk::Geo<S>::SL0 slices of a stage, pass 1
+// all of them).
 template <int S>
-int launch_products(const CUtensorMap& mapA, const CUtensorMap& mapB, const Grid& g,
-                    int64_t njobs, long long* part, int* status, cudaStream_t s) {
+int launch_products(const OzSlices& A, const OzSlices& B, const Grid& g, int64_t njobs,
+                    long long* part, int* status, cudaStream_t s) {
+  if (g.tn == nk::TN) {
+    CUtensorMap mA, mB;
+    TK_TRY(make_slice_map(&mA, A, TM, S));
+    TK_TRY(make_slice_map(&mB, B, nk::TN, S));
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        nk::gram_ozaki_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        nk::Geo<S>::SMEM_BYTES);
+    TK_CUDA(attr);
+    nk::gram_ozaki_kernel<S><<<(unsigned)njobs, nk::NTHREADS, nk::Geo<S>::SMEM_BYTES, s>>>(
+        mA, mB, g, part, status);
+    TK_LAUNCH();
+    return TUCKER_OK;
+  }
+  CUtensorMap mA0, mB0, mA1, mB1;
+  TK_TRY(make_slice_map(&mA0, A, TM, wk::Geo<S>::SL0));
+  TK_TRY(make_slice_map(&mB0, B, wk::TN, wk::Geo<S>::SL0));
+  TK_TRY(make_slice_map(&mA1, A, TM, wk::Geo<S>::SL1));
+  TK_TRY(make_slice_map(&mB1, B, wk::TN, wk::Geo<S>::SL1));
   static const cudaError_t attr = cudaFuncSetAttribute(
-      gram_ozaki_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<S>::SMEM_BYTES);
+      wk::gram_ozaki_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      wk::Geo<S>::SMEM_BYTES);
   TK_CUDA(attr);
-  gram_ozaki_kernel<S><<<(unsigned)njobs, NTHREADS, Geo<S>::SMEM_BYTES, s>>>(mapA, mapB, g, part,
-                                                                             status);
+  wk::gram_ozaki_kernel<S><<<(unsigned)njobs, wk::NTHREADS, wk::Geo<S>::SMEM_BYTES, s>>>(
+      mA0, mB0, mA1, mB1, g, part, status);
   TK_LAUNCH();
   return TUCKER_OK;
 }
@@ -657,10 +1007,14 @@ int oz_gemm_nt(const OzSlices& A, const OzSlices& B, bool sym, double alpha, dou
   if (A.ldK != B.ldK || A.nslice != B.nslice || (sym && &A != &B)) return TUCKER_EINVAL;
   const int S = A.nslice;
   const int m = A.rows, n = B.rows;
+  // The long symmetric Grams take 128 x 128 tiles (half the MMA instructions per output); the
+  // eigensolver's products, whose B has ~150 columns, waste less with 128 x 64.
+  const int TN = (sym && S == OZ_GRAM_SLICES) ? wk::TN : nk::TN;
   const int nti = ceil_div(m, TM), ntj = ceil_div(n, TN);
   const int nst = (int)(A.ldK / KS);
-  Grid g{ntj, 0, 1, nst, sym ? 1 : 0, nullptr};
-  g.npairs = sym ? nti * (nti + 1) - (ntj < 2 * nti ? 1 : 0) : nti * ntj;
+  Grid g{ntj, 0, 1, nst, sym ? 1 : 0, TN, nullptr};
+  g.npairs = !sym ? nti * ntj
+             : TN == nk::TN ? nti * (nti + 1) - (ntj < 2 * nti ? 1 : 0) : nti * (nti + 1) / 2;
   // K splits: the fewest that fill the SMs' waves to 90 %, each at least 8 stages long and at
   // most MAX_JOB_STAGES.
   const int sms = num_sms();
@@ -690,9 +1044,6 @@ int oz_gemm_nt(const OzSlices& A, const OzSlices& B, bool sym, double alpha, dou
     TK_LAUNCH();
     return TUCKER_OK;
   }
-  CUtensorMap mapA, mapB;
-  TK_TRY(make_slice_map(&mapA, A, TM));
-  TK_TRY(make_slice_map(&mapB, B, TN));
   Buf part;
   TK_TRY(part.alloc(sizeof(long long) * 2 * TM * TN * (size_t)njobs, s));
   {
@@ -703,11 +1054,11 @@ int oz_gemm_nt(const OzSlices& A, const OzSlices& B, bool sym, double alpha, dou
                  2.0 * S * ((double)A.rows_pad + (sym ? 0.0 : (double)B.rows_pad)) * A.ldK +
                      16.0 * TM * TN * (double)njobs);
     if (S == 7)
-      TK_TRY(launch_products<7>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
+      TK_TRY(launch_products<7>(A, B, g, njobs, part.as<long long>(), status, s));
     else if (S == 6)
-      TK_TRY(launch_products<6>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
+      TK_TRY(launch_products<6>(A, B, g, njobs, part.as<long long>(), status, s));
     else
-      TK_TRY(launch_products<3>(mapA, mapB, g, njobs, part.as<long long>(), status, s));
+      TK_TRY(launch_products<3>(A, B, g, njobs, part.as<long long>(), status, s));
   }
   oz_reduce<<<ceil_div((int64_t)m * n, 256), 256, 0, s>>>(part.as<long long>(), g, S, m, n,
                                                            A.ex.as<int>(), B.ex.as<int>(), alpha,
@@ -790,6 +1141,7 @@ __global__ void oz_reduce_batched(const long long* __restrict__ partial, int ntj
                                   int nslice, int64_t nslices, int Jm, int Jo,
                                   const int* __restrict__ exA, const int* __restrict__ exB,
                                   double* __restrict__ Y) {
+  constexpr int TN = nk::TN;   // the batched products use 128 x 64 tiles
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t per = (int64_t)Jm * Jo;
   if (t >= nslices * per) return;
@@ -833,6 +1185,7 @@ int ttmc_f64_tc(const tucker_tensor_s* X, const Ordering* o, const double* Um, i
                 const double* Uo, int Jo, double* Y, cudaStream_t s) {
   const int64_t In = X->dims[o->n], F = o->F;
   constexpr int S = OZ_GRAM_SLICES;
+  constexpr int TN = nk::TN;   // short per-slice products: 128 x 64 tiles in one pass
   if (In == 0) return TUCKER_OK;
   ProfScope prof("ttmc_f64_tc", s, 2.0 * ((double)X->nnz * Jo + (double)F * Jm * Jo),
                  12.0 * X->nnz + 16.0 * F + 8.0 * In * (double)Jm * Jo);
@@ -894,19 +1247,16 @@ int ttmc_f64_tc(const tucker_tensor_s* X, const Ordering* o, const double* Um, i
   }
   // one product per slice: (J_m x J_o) = A_i^T B_i over the slice's stages
   const int nti = ceil_div(Jm, TM), ntj = ceil_div(Jo, TN);
-  Grid g{ntj, nti * ntj, 1, (int)stages, 0, sst.as<int>()};
+  Grid g{ntj, nti * ntj, 1, (int)stages, 0, TN, sst.as<int>()};
   const int64_t njobs = In * g.npairs;
   TK_TRY(part.alloc(sizeof(long long) * 2 * TM * TN * (size_t)njobs, s));
   TK_TRY(st.alloc(sizeof(int), s));
   TK_CUDA(cudaMemsetAsync(st.p, 0, sizeof(int), s));
-  CUtensorMap mapA, mapB;
-  TK_TRY(make_slice_map(&mapA, A, TM));
-  TK_TRY(make_slice_map(&mapB, B, TN));
   {
     ProfScope pk("ttmc_ozaki", s,
-                 2.0 * Geo<S>::PAIRS * TM * TN * (double)KS * stages * g.npairs,
+                 2.0 * nk::Geo<S>::PAIRS * TM * TN * (double)KS * stages * g.npairs,
                  2.0 * S * ((double)A.rows_pad + B.rows_pad) * ldK + 16.0 * TM * TN * (double)njobs);
-    TK_TRY(launch_products<S>(mapA, mapB, g, njobs, part.as<long long>(), st.as<int>(), s));
+    TK_TRY(launch_products<S>(A, B, g, njobs, part.as<long long>(), st.as<int>(), s));
   }
   oz_reduce_batched<<<ceil_div(In * Jm * Jo, 256), 256, 0, s>>>(
       part.as<long long>(), ntj, g.npairs, S, In, Jm, Jo, A.ex.as<int>(), B.ex.as<int>(), Y);
