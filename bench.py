@@ -185,8 +185,9 @@ KERNELS = ("gram_ozaki", "gemm_ozaki", "eig_mv_ozaki", "eig_mv_ozaki3", "eig_tn_
            "ttmc_ozaki", "ozaki_split", "syrk_f64", "gram_bf16x3", "gram_fused", "ttmc_f64",
            "ttmc_mixed", "slice_proj_f64", "slice_proj_mixed", "unfold_gram_f64", "gemm_nn_f64",
            "gemm_nn_f32", "gemm_tn_f64", "chol_f64", "jacobi_f64", "csf_build")
-# DRAM bytes / algorithmic bytes of gram_ozaki_kernel<6> on the 500^3 MP Gram (one ncu capture)
-GRAM_OZAKI_DRAM_RATIO = (310.36e6 + 3.75e6) / (2 * 6 * 512 * 50048 + 16 * 128 * 64 * 140)
+# DRAM bytes / algorithmic bytes of the 128 x 128 two-pass gram_ozaki kernel on the 500^3 MP Gram
+# (one ncu capture): the second pass reads slices 0-3 again from DRAM
+GRAM_OZAKI_DRAM_RATIO = (522.44e6 + 33.47e6) / (2 * 6 * 512 * 50048 + 16 * 128 * 128 * 140)
 # FP64 products on the BF16 tensor cores (their FLOPs are the BF16 FLOPs issued)
 OZAKI_KERNELS = ("gram_ozaki", "gemm_ozaki", "eig_mv_ozaki", "eig_mv_ozaki3", "eig_tn_ozaki",
                  "ttmc_ozaki")
@@ -687,12 +688,14 @@ def main():
                                "issue (22 or 28 slice products per FP64 product)")
         if roofline and dom == "gram_ozaki":
             # DRAM bytes of one ncu capture of this kernel on the 500^3 MP Gram (rows 500,
-            # K = 5e4): 0.964 of its algorithmic bytes (slices read once from DRAM, partials
-            # left in L2).  The slice bytes grow with rows x K, so the ratio scales to the bench
-            # launches; the capture of the full-size launch is above the size ncu may take.
+            # K = 5e4): 1.62 x its algorithmic bytes (the slices once, plus slices 0-3 again in
+            # the second pass, plus the int64 partials).  The slice bytes grow with rows x K, so
+            # the ratio scales to the bench launches; the capture of the full-size launch is above
+            # the size ncu may take.
             roofline["traffic"] = GRAM_OZAKI_DRAM_RATIO * roofline["algorithmic_bytes"]
             roofline["traffic_note"] = ("per launch, scaled from an ncu capture of the 500^3 "
-                                        "MP Gram (DRAM bytes 0.964 x algorithmic)")
+                                        "MP Gram (DRAM bytes 1.62 x algorithmic: the second "
+                                        "pass re-reads slices 0-3)")
     else:
         roofline = roofline_of(prof, dom, prof_ms, "alu", FP64_PEAK_TFLOPS, "TFLOP/s", fp64_src)
     mx_gram = roofline_of(mx_prof, "gram_bf16x3", mx_prof_ms, "tensor", bf16, "TFLOP/s", bf16_src)
