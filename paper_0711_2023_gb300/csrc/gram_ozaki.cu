@@ -1102,8 +1102,9 @@ namespace {
 // Slices of a gathered, transposed operand for the batched HOOI projection: the K position of
 // fiber f is pos(f) = f + pad[slice of f] (every slice's fibers start on a stage boundary);
 // out[s][j][pos(f)] = digit s of S[src(f)][j] scaled by 2^-ex[j] (src(f) = rows[f], or f when
-// rows is NULL), for j < J.  Positions not written stay zero (the buffer is cleared first).
-// Tiles of 32 fibers x 32 columns through shared memory keep reads and writes coalesced.
+// rows is NULL) for j < J, and 0 for J <= j < rows_pad (grid.y = rows_pad / 32).  The positions
+// of no fiber (the tail of each slice's last stage) are cleared by oz_zero_tails.  Tiles of
+// 32 fibers x 32 columns through shared memory keep reads and writes coalesced.
 template <int S>
 __global__ void oz_split_gather_kernel(const double* __restrict__ Src, int64_t ld, int J,
                                        const int32_t* __restrict__ rows, int64_t F,
@@ -1131,8 +1132,26 @@ __global__ void oz_split_gather_kernel(const double* __restrict__ Src, int64_t l
   if (pos < 0) return;
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int j = j0 + i;
-    if (j >= J) continue;
-    oz_cut<S>(oz_fixed<S>(tile[threadIdx.x][i], ex[j]), Q + (int64_t)j * ldK + pos, plane);
+    oz_cut<S>(j < J ? oz_fixed<S>(tile[threadIdx.x][i], ex[j]) : 0ll, Q + (int64_t)j * ldK + pos,
+              plane);
+  }
+}
+
+// Zeros at the positions of no fiber: slice i's fibers fill [sst[i] 32, sst[i] 32 + F_i) of its
+// stages [sst[i], sst[i + 1]); the rest (at most 31 columns) of every row and slice plane.
+__global__ void oz_zero_tails(const int64_t* __restrict__ root_ptr, const int* __restrict__ sst,
+                              int rows_pad, int64_t ldK, int nslice,
+                              __nv_bfloat16* __restrict__ Q) {
+  const int64_t i = blockIdx.x;
+  const int64_t a = (int64_t)sst[i] * KS + (root_ptr[i + 1] - root_ptr[i]);
+  const int len = (int)((int64_t)sst[i + 1] * KS - a);
+  if (len <= 0) return;
+  const int64_t plane = (int64_t)rows_pad * ldK;
+  __nv_bfloat16_raw z;
+  z.x = 0;
+  for (int t = threadIdx.x; t < nslice * rows_pad * len; t += blockDim.x) {
+    const int c = t % len, r = (t / len) % rows_pad, sl = t / (len * rows_pad);
+    Q[(int64_t)sl * plane + (int64_t)r * ldK + a + c] = z;
   }
 }
 
@@ -1172,7 +1191,7 @@ template <int S>
 int split_gather(const double* Src, int64_t ld, int J, const int32_t* rows, int64_t F,
                  const int32_t* fiber_root, const int64_t* pad, const int* ex, int rows_pad,
                  int64_t ldK, __nv_bfloat16* Q, cudaStream_t s) {
-  dim3 grid((unsigned)ceil_div(F, 32), (unsigned)ceil_div(J, 32));
+  dim3 grid((unsigned)ceil_div(F, 32), (unsigned)(rows_pad / 32));
   oz_split_gather_kernel<S><<<grid, dim3(32, 8), 0, s>>>(Src, ld, J, rows, F, fiber_root, pad, ex,
                                                          rows_pad, ldK, Q);
   TK_LAUNCH();
@@ -1222,8 +1241,17 @@ int ttmc_f64_tc(const tucker_tensor_s* X, const Ordering* o, const double* Um, i
   TK_TRY(B.Q.alloc(sizeof(__nv_bfloat16) * S * (size_t)B.rows_pad * ldK, s));
   TK_TRY(A.ex.alloc(sizeof(int) * A.rows_pad, s));
   TK_TRY(B.ex.alloc(sizeof(int) * B.rows_pad, s));
-  TK_CUDA(cudaMemsetAsync(A.Q.p, 0, A.Q.bytes, s));
-  TK_CUDA(cudaMemsetAsync(B.Q.p, 0, B.Q.bytes, s));
+  if (F == 0) {   // no fiber: every position is padding
+    TK_CUDA(cudaMemsetAsync(A.Q.p, 0, A.Q.bytes, s));
+    TK_CUDA(cudaMemsetAsync(B.Q.p, 0, B.Q.bytes, s));
+  } else {
+    oz_zero_tails<<<(unsigned)In, 256, 0, s>>>(o->root_ptr, sst.as<int>(), A.rows_pad, ldK, S,
+                                                A.Q.as<__nv_bfloat16>());
+    TK_LAUNCH();
+    oz_zero_tails<<<(unsigned)In, 256, 0, s>>>(o->root_ptr, sst.as<int>(), B.rows_pad, ldK, S,
+                                                B.Q.as<__nv_bfloat16>());
+    TK_LAUNCH();
+  }
   TK_CUDA(cudaMemsetAsync(A.ex.p, 0x80, sizeof(int) * Jm, s));
   TK_CUDA(cudaMemsetAsync(B.ex.p, 0x80, sizeof(int) * Jo, s));
   const int64_t Im = X->dims[o->m];
