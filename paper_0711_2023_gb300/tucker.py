@@ -763,6 +763,10 @@ def tucker_stream_create(idx, val, dims, budget) -> StreamTensor:
     return StreamTensor(h, dims)
 
 
+def tucker_stream_destroy(X: StreamTensor):
+    X.close()
+
+
 def tucker_stream_info(X: StreamTensor):
     nnz, n2, ch = c_int64(), c_double(), c_int64()
     _check(_lib().tucker_stream_info(X.handle, ctypes.byref(nnz), ctypes.byref(n2),
