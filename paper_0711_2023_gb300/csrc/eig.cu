@@ -336,59 +336,97 @@ chol_inv_kernel(const double* __restrict__ G, int k, double shift, double* __res
   }
 }
 
-// Cholesky G + shift I = R^T R without the inverse, for Cholesky-QR by triangular solves.
-// A G within 2^-27 of the identity takes the first-order factor (below).  Otherwise
-// right-looking, one CTA: step j updates the trailing upper triangle with the unscaled row j,
-// R[r][c] -= R[j][r] R[j][c] / d_j, and rows are scaled by 1/sqrt(d_j) once at the end.  One
-// thread forms each pivot's reciprocal square root (FP64 square roots and divisions are long
-// instruction sequences on this part).  The work array is shared memory for k <= CHOL_SMEM_MAX_K
-// and Rout itself otherwise.  A non-positive pivot restarts the factorisation once with the
-// shift 11 (n k + k (k + 1)) eps tr(G) (shifted Cholesky-QR, Fukaya et al. 2020) and sets
+// Cholesky G + shift I = R^T R without the inverse, for Cholesky-QR by triangular solves
+// (k <= TRSM_MAX_K), spread over one cluster of CHOL_CL CTAs.  FP64 arithmetic issues at a few
+// lanes per cycle per SM on this part, so a factorisation on one SM is bound by that rate; the
+// cluster multiplies it by CHOL_CL.  R is built in place in Rout (global memory, L2-resident).
+//   A G within 2^-27 of the identity takes the first-order factor R = I + triu(F, 1) + diag(F)/2
+// (G = I + F; exact to O(|F|^2) < eps) with no serial factorisation.
+//   Otherwise right-looking by blocks of CHOL_NB rows.  For block row J (rows J0..J1-1):
+//   1. every CTA factors the diagonal block and its own share of the panel columns (columns
+//      J1 + b + CHOL_CL s for CTA b), one element of the block row per thread, by jb unscaled
+//      elimination steps a[r][c] -= a[j][r] a[j][c] / d_j; the diagonal block is factored
+//      redundantly by every CTA from identical data, so all CTAs take the same branches.  Row j+1
+//      is published in shared memory as soon as step j has finished it; the thread holding the
+//      next pivot forms its reciprocal (recip_newton).  The rows are then scaled by
+//      1 / sqrt(d_r) and the panel written back;
+//   2. after a cluster barrier every CTA reads the whole panel P (jb x m) and the trailing upper
+//      triangle takes W[q][c] -= sum_i P[i][q] P[i][c], its elements spread over all threads of
+//      the cluster (rows q and m - 1 - q folded together so that every fold has m + 1 elements);
+//      CTA 0 stores the diagonal block; a second cluster barrier ends the block.
+// A non-positive pivot restarts the factorisation once with the shift
+// 11 (n k + k (k + 1)) eps tr(G) (shifted Cholesky-QR, Fukaya et al. 2020) and sets
 // DEV_CHOL_SHIFTED; if that fails too, DEV_CHOL_BREAKDOWN.  Outputs: R (k x k, upper, zero
 // below) and rdinv[j] = 1 / R[j][j].
-constexpr int CHOL_SMEM_MAX_K = 160;
 constexpr int TRSM_MAX_K = 384;
+constexpr int CHOL_CL = 8;
+constexpr int CHOL_NB = 16;
+constexpr int CHOL_THREADS = 512;
+constexpr int CHOL_SLOTS = 2;  // block-row elements per thread: jb (jb + 1) / 2 + jb ceil(m / CL)
+static_assert(CHOL_NB * (CHOL_NB + 1) / 2 +
+                  CHOL_NB * ((TRSM_MAX_K - CHOL_NB + CHOL_CL - 1) / CHOL_CL) <=
+              CHOL_SLOTS * CHOL_THREADS, "block row does not fit the CTA");
 
-__global__ void __launch_bounds__(1024)
-chol_kernel(const double* __restrict__ G, int k, int64_t nrows, double* __restrict__ Rout,
-            double* __restrict__ rdinv, int* __restrict__ status) {
-  extern __shared__ double shm[];
-  __shared__ double dinv_s, shift_s;
-  __shared__ int bad_s;
-  const bool in_smem = k <= CHOL_SMEM_MAX_K;
-  double* R = in_smem ? shm : Rout;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  // Near-identity fast path (the second pass of Cholesky-QR): for G = I + F with max |F| below
-  // 2^-27, R = I + triu(F, 1) + diag(F) / 2 is exact to O(|F|^2) < eps, with no serial
-  // factorisation.  max |F| is taken over the bit patterns (no FP64 compares).
+// 1 / d for a normal d > 0: a seed from the FP32 reciprocal of d's leading mantissa bits
+// (relative error below 2^-22, formed with integer operations and one rcp.approx), then two
+// Newton-Raphson steps x <- x + x (1 - d x), each squaring the relative error, to FP64 rounding
+// level.  Exponents outside [1, 2044] take the division.
+__device__ __forceinline__ double recip_newton(double d) {
+  const long long bits = __double_as_longlong(d);
+  const int e = (int)((bits >> 52) & 0x7ff);
+  if (e < 1 || e > 2044) return 1.0 / d;
+  const unsigned fm = 0x3f800000u | (unsigned)((bits >> 29) & 0x7fffff);  // mantissa in [1, 2)
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__uint_as_float(fm)));
+  const unsigned yb = __float_as_uint(y);                                  // y in (0.5, 1]
+  const long long ye = (long long)((yb >> 23) & 0xff) - 127 + 1023 + (1023 - e);
+  double x = __longlong_as_double((ye << 52) | ((long long)(yb & 0x7fffff) << 29));
+  double r = fma(-d, x, 1.0);
+  x = fma(x, r, x);
+  r = fma(-d, x, 1.0);
+  return fma(x, r, x);
+}
+
+__global__ void __launch_bounds__(CHOL_THREADS)
+chol_cluster_kernel(const double* __restrict__ G, int k, int64_t nrows, double* Rout,
+                    double* __restrict__ rdinv, int* __restrict__ status) {
+  extern __shared__ double panel[];  // jb x m, row stride m
+  __shared__ double rowbuf[2][CHOL_NB + 48];
+  __shared__ double dinv_s[2];
+  __shared__ double piv_s[CHOL_NB], ri_s[CHOL_NB];
+  __shared__ double shift_s;
+  __shared__ unsigned long long fmax_s;
+  double* W = Rout;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int gtid = b * CHOL_THREADS + tid, gthreads = CHOL_CL * CHOL_THREADS;
+  const int64_t kk = (int64_t)k * k;
   {
-    __shared__ unsigned long long fmax_s;
     if (tid == 0) fmax_s = 0ull;
     __syncthreads();
     unsigned long long mb = 0ull;
-    for (int r = warp; r < k; r += nw)
-      for (int c = r + lane; c < k; c += 32) {
-        const double f = G[(int64_t)r * k + c] - (c == r ? 1.0 : 0.0);
-        const unsigned long long b =
-            (unsigned long long)__double_as_longlong(f) & 0x7fffffffffffffffull;
-        mb = b > mb ? b : mb;
-      }
+    for (int64_t t = tid; t < kk; t += CHOL_THREADS) {
+      const int r = (int)(t / k), c = (int)(t % k);
+      if (c < r) continue;
+      const double f = G[t] - (c == r ? 1.0 : 0.0);
+      const unsigned long long bb =
+          (unsigned long long)__double_as_longlong(f) & 0x7fffffffffffffffull;
+      mb = bb > mb ? bb : mb;
+    }
     atomicMax(&fmax_s, mb);
     __syncthreads();
     if (__longlong_as_double((long long)fmax_s) <= 7.450580596923828e-9) {
-      for (int r = warp; r < k; r += nw) {
+      for (int64_t t = gtid; t < kk; t += gthreads) {
+        const int r = (int)(t / k), c = (int)(t % k);
         const double drr = 0.5 * (1.0 + G[(int64_t)r * k + r]);
-        if (lane == 0) rdinv[r] = 1.0 / drr;
-        for (int c = lane; c < k; c += 32)
-          Rout[(int64_t)r * k + c] = c > r ? G[(int64_t)r * k + c] : (c == r ? drr : 0.0);
+        W[t] = c > r ? G[t] : (c == r ? drr : 0.0);
+        if (c == r) rdinv[r] = 1.0 / drr;
       }
-      return;
+      return;  // uniform over the cluster: every CTA read the same G
     }
   }
   int attempt = 0;
   for (; attempt < 2; ++attempt) {
     if (tid == 0) {
-      bad_s = 0;
       double sh = 0.0;
       if (attempt == 1) {
         double tr = 0.0;
@@ -399,44 +437,120 @@ chol_kernel(const double* __restrict__ G, int k, int64_t nrows, double* __restri
     }
     __syncthreads();
     const double shift = shift_s;
-    for (int r = warp; r < k; r += nw)
-      for (int c = lane; c < k; c += 32)
-        R[(int64_t)r * k + c] = c >= r ? G[(int64_t)r * k + c] + (c == r ? shift : 0.0) : 0.0;
-    __syncthreads();
-    for (int j = 0; j < k; ++j) {
-      if (tid == 0) {
-        const double d = R[(int64_t)j * k + j];
-        if (!(d > 0.0)) {
-          bad_s = 1;
-        } else {
-          const double ri = rsqrt(d);
-          rdinv[j] = ri;
-          dinv_s = ri * ri;
+    for (int64_t t = gtid; t < kk; t += gthreads) {
+      const int r = (int)(t / k), c = (int)(t % k);
+      W[t] = c >= r ? G[t] + (c == r ? shift : 0.0) : 0.0;
+    }
+    cluster_round_barrier();
+    bool bad = false;
+    for (int J0 = 0; J0 < k; J0 += CHOL_NB) {
+      const int jb = min(CHOL_NB, k - J0), J1 = J0 + jb, m = k - J1;
+      const int nc = m > b ? (m - b + CHOL_CL - 1) / CHOL_CL : 0;
+      const int nelem = jb * nc + jb * (jb + 1) / 2;
+      // This thread's elements of the block row: row r, rowbuf slot x (x < CHOL_NB: diagonal
+      // column J0 + x; otherwise panel column J1 + b + CHOL_CL (x - CHOL_NB)).
+      int er[CHOL_SLOTS], ex[CHOL_SLOTS];
+      double a[CHOL_SLOTS];
+#pragma unroll
+      for (int e = 0; e < CHOL_SLOTS; ++e) {
+        const int idx = tid + e * CHOL_THREADS;
+        er[e] = -1;
+        ex[e] = 0;
+        a[e] = 0.0;
+        if (idx < nelem) {
+          int rem = idx;
+          for (int rr = 0; rr < jb; ++rr) {
+            const int len = jb - rr + nc;
+            if (rem < len) {
+              er[e] = rr;
+              ex[e] = rem < jb - rr ? rr + rem : CHOL_NB + rem - (jb - rr);
+              break;
+            }
+            rem -= len;
+          }
+          const int col = ex[e] < CHOL_NB ? J0 + ex[e] : J1 + b + CHOL_CL * (ex[e] - CHOL_NB);
+          a[e] = __ldcg(W + (int64_t)(J0 + er[e]) * k + col);
+          if (er[e] == 0) {
+            rowbuf[0][ex[e]] = a[e];
+            if (ex[e] == 0) {
+              piv_s[0] = a[e];
+              dinv_s[0] = recip_newton(a[e]);
+            }
+          }
         }
       }
+      for (int j = 0; j < jb; ++j) {
+        __syncthreads();
+        const double d = rowbuf[j & 1][j];
+        if (!(d > 0.0)) {  // every thread of every CTA reads the same pivot
+          bad = true;
+          break;
+        }
+        const double dinv = dinv_s[j & 1];
+#pragma unroll
+        for (int e = 0; e < CHOL_SLOTS; ++e) {
+          if (er[e] > j) {
+            const double f = rowbuf[j & 1][er[e]] * dinv;
+            a[e] = fma(-f, rowbuf[j & 1][ex[e]], a[e]);
+            if (er[e] == j + 1) {
+              rowbuf[(j + 1) & 1][ex[e]] = a[e];
+              if (ex[e] == j + 1) {
+                piv_s[j + 1] = a[e];
+                dinv_s[(j + 1) & 1] = recip_newton(a[e]);
+              }
+            }
+          }
+        }
+      }
+      if (bad) break;
       __syncthreads();
-      if (bad_s) break;  // read by all threads after the barrier: uniform
-      const double dinv = dinv_s;
-      const double* Rj = R + (int64_t)j * k;
-      for (int r = j + 1 + warp; r < k; r += nw) {
-        const double f = Rj[r] * dinv;
-        double* Rr = R + (int64_t)r * k;
-        for (int c = r + lane; c < k; c += 32) Rr[c] = fma(-f, Rj[c], Rr[c]);
+      if (tid < jb) ri_s[tid] = rsqrt(piv_s[tid]);
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < CHOL_SLOTS; ++e) {
+        if (er[e] >= 0) {
+          a[e] *= ri_s[er[e]];
+          if (ex[e] >= CHOL_NB)
+            W[(int64_t)(J0 + er[e]) * k + J1 + b + CHOL_CL * (ex[e] - CHOL_NB)] = a[e];
+        }
+      }
+      if (b == 0 && tid < jb) rdinv[J0 + tid] = ri_s[tid];
+      cluster_round_barrier();
+      for (int t = tid; t < jb * m; t += CHOL_THREADS) {
+        const int i = t / m, c = t % m;
+        panel[t] = __ldcg(W + (int64_t)(J0 + i) * k + J1 + c);
+      }
+      if (b == 0) {
+#pragma unroll
+        for (int e = 0; e < CHOL_SLOTS; ++e)
+          if (er[e] >= 0 && ex[e] < CHOL_NB) W[(int64_t)(J0 + er[e]) * k + J0 + ex[e]] = a[e];
       }
       __syncthreads();
+      const int m1 = m + 1;
+      const int total = ((m + 1) / 2) * m1;
+      for (int f = gtid; f < total; f += gthreads) {
+        const int p = f / m1, xx = f % m1;
+        int q = p, c = p + xx;
+        if (xx >= m - p) {
+          q = m - 1 - p;
+          if (q == p) continue;
+          c = q + xx - (m - p);
+        }
+        double* w = W + (int64_t)(J1 + q) * k + J1 + c;
+        double acc = __ldcg(w);
+#pragma unroll
+        for (int i = 0; i < CHOL_NB; ++i)
+          if (i < jb) acc = fma(-panel[i * m + q], panel[i * m + c], acc);
+        *w = acc;
+      }
+      cluster_round_barrier();
     }
-    if (!bad_s) break;
-    __syncthreads();
+    if (!bad) break;
+    cluster_round_barrier();  // every CTA has stopped reading W before the restart rewrites it
   }
-  if (attempt == 2) {
-    if (tid == 0) atomicOr(status, DEV_CHOL_BREAKDOWN);
-    return;
-  }
-  if (attempt == 1 && tid == 0) atomicOr(status, DEV_CHOL_SHIFTED);
-  for (int r = warp; r < k; r += nw) {
-    const double ri = rdinv[r];
-    for (int c = lane; c < k; c += 32)
-      Rout[(int64_t)r * k + c] = c >= r ? R[(int64_t)r * k + c] * ri : 0.0;
+  if (b == 0 && tid == 0) {
+    if (attempt == 2) atomicOr(status, DEV_CHOL_BREAKDOWN);
+    else if (attempt == 1) atomicOr(status, DEV_CHOL_SHIFTED);
   }
 }
 
@@ -851,12 +965,24 @@ int cholqr_pass(EigOps& e, double* V, int64_t ldv, int n, int k, const CholWork&
   TK_TRY(op_tn(e, k, k, n, V, ldv, V, ldv, w.Gk, k));
   {
     ProfScope prof("chol_f64", s, (double)k * k * k / 3.0, 0.0);
+    constexpr int max_smem = (int)(sizeof(double) * CHOL_NB * (TRSM_MAX_K - 1));
     static const cudaError_t attr = cudaFuncSetAttribute(
-        chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)(sizeof(double) * CHOL_SMEM_MAX_K * CHOL_SMEM_MAX_K));
+        chol_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     TK_CUDA(attr);
-    const size_t smem = k <= CHOL_SMEM_MAX_K ? sizeof(double) * (size_t)k * k : 0;
-    chol_kernel<<<1, 1024, smem, s>>>(w.Gk, k, n, w.R, w.rd, stat);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CHOL_CL, 1, 1);
+    cfg.blockDim = dim3(CHOL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = sizeof(double) * CHOL_NB * (size_t)std::max(k - 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute cl[1];
+    cl[0].id = cudaLaunchAttributeClusterDimension;
+    cl[0].val.clusterDim.x = CHOL_CL;
+    cl[0].val.clusterDim.y = 1;
+    cl[0].val.clusterDim.z = 1;
+    cfg.attrs = cl;
+    cfg.numAttrs = 1;
+    TK_CUDA(cudaLaunchKernelEx(&cfg, chol_cluster_kernel, (const double*)w.Gk, k, (int64_t)n,
+                               w.R, w.rd, stat));
   }
   TK_LAUNCH();
   return trsm_rows(V, ldv, n, k, w.R, w.rd, stat, s);
