@@ -337,14 +337,16 @@ chol_inv_kernel(const double* __restrict__ G, int k, double shift, double* __res
 }
 
 // Cholesky G + shift I = R^T R without the inverse, for Cholesky-QR by triangular solves
-// (k <= TRSM_MAX_K), spread over one cluster of CHOL_CL CTAs.  FP64 arithmetic issues at a few
-// lanes per cycle per SM on this part, so a factorisation on one SM is bound by that rate; the
-// cluster multiplies it by CHOL_CL.  R is built in place in Rout (global memory, L2-resident).
+// (k <= TRSM_MAX_K), spread over one cluster of CL CTAs (16 where the GPU can co-schedule them,
+// else 8).  FP64 arithmetic on this part retires under two lanes per cycle per SM with a 64-cycle
+// dependent latency, so a factorisation on one SM is bound by that rate; the cluster multiplies
+// it by CL, and the serial pivot chain is kept to five dependent FP64 operations per pivot.  R is
+// built in place in Rout (global memory, L2-resident).
 //   A G within 2^-27 of the identity takes the first-order factor R = I + triu(F, 1) + diag(F)/2
 // (G = I + F; exact to O(|F|^2) < eps) with no serial factorisation.
 //   Otherwise right-looking by blocks of CHOL_NB rows.  For block row J (rows J0..J1-1):
 //   1. every CTA factors the diagonal block and its own share of the panel columns (columns
-//      J1 + b + CHOL_CL s for CTA b), one element of the block row per thread, by jb unscaled
+//      J1 + b + CL s for CTA b), one element of the block row per thread, by jb unscaled
 //      elimination steps a[r][c] -= a[j][r] a[j][c] / d_j; the diagonal block is factored
 //      redundantly by every CTA from identical data, so all CTAs take the same branches.  Row j+1
 //      is published in shared memory as soon as step j has finished it; the thread holding the
@@ -359,18 +361,26 @@ chol_inv_kernel(const double* __restrict__ G, int k, double shift, double* __res
 // DEV_CHOL_SHIFTED; if that fails too, DEV_CHOL_BREAKDOWN.  Outputs: R (k x k, upper, zero
 // below) and rdinv[j] = 1 / R[j][j].
 constexpr int TRSM_MAX_K = 384;
-constexpr int CHOL_CL = 8;
 constexpr int CHOL_NB = 16;
 constexpr int CHOL_THREADS = 512;
-constexpr int CHOL_SLOTS = 2;  // block-row elements per thread: jb (jb + 1) / 2 + jb ceil(m / CL)
-static_assert(CHOL_NB * (CHOL_NB + 1) / 2 +
-                  CHOL_NB * ((TRSM_MAX_K - CHOL_NB + CHOL_CL - 1) / CHOL_CL) <=
-              CHOL_SLOTS * CHOL_THREADS, "block row does not fit the CTA");
+// Block-row elements per thread: jb (jb + 1) / 2 + jb ceil(m / CL) over CHOL_THREADS threads.
+template <int CL>
+__host__ __device__ constexpr int chol_slots() {
+  return (CHOL_NB * (CHOL_NB + 1) / 2 + CHOL_NB * ((TRSM_MAX_K - CHOL_NB + CL - 1) / CL) +
+          CHOL_THREADS - 1) / CHOL_THREADS;
+}
 
-// 1 / d for a normal d > 0: a seed from the FP32 reciprocal of d's leading mantissa bits
-// (relative error below 2^-22, formed with integer operations and one rcp.approx), then two
-// Newton-Raphson steps x <- x + x (1 - d x), each squaring the relative error, to FP64 rounding
-// level.  Exponents outside [1, 2044] take the division.
+// d > 0 (and not NaN) decided on the bit pattern with integer compares.
+__device__ __forceinline__ bool positive_f64(double d) {
+  const long long bits = __double_as_longlong(d);
+  return bits > 0 && bits <= 0x7ff0000000000000ll;
+}
+
+// 1 / d for a normal d > 0: a seed x from the FP32 reciprocal of d's leading mantissa bits
+// (relative error below 2^-22, formed with integer operations and one rcp.approx), then one
+// third-order step x <- x (1 + e + e^2) with e = 1 - d x, which cubes the relative error (the
+// Newton-Raphson step x (1 + e) only squares it), to FP64 rounding level in three dependent FMAs.
+// Exponents outside [1, 2044] take the division.
 __device__ __forceinline__ double recip_newton(double d) {
   const long long bits = __double_as_longlong(d);
   const int e = (int)((bits >> 52) & 0x7ff);
@@ -381,12 +391,11 @@ __device__ __forceinline__ double recip_newton(double d) {
   const unsigned yb = __float_as_uint(y);                                  // y in (0.5, 1]
   const long long ye = (long long)((yb >> 23) & 0xff) - 127 + 1023 + (1023 - e);
   double x = __longlong_as_double((ye << 52) | ((long long)(yb & 0x7fffff) << 29));
-  double r = fma(-d, x, 1.0);
-  x = fma(x, r, x);
-  r = fma(-d, x, 1.0);
-  return fma(x, r, x);
+  const double e1 = fma(-d, x, 1.0);
+  return fma(x, fma(e1, e1, e1), x);
 }
 
+template <int CL>
 __global__ void __launch_bounds__(CHOL_THREADS)
 chol_cluster_kernel(const double* __restrict__ G, int k, int64_t nrows, double* Rout,
                     double* __restrict__ rdinv, int* __restrict__ status) {
@@ -398,28 +407,38 @@ chol_cluster_kernel(const double* __restrict__ G, int k, int64_t nrows, double* 
   __shared__ unsigned long long fmax_s;
   double* W = Rout;
   const int b = blockIdx.x, tid = threadIdx.x;
-  const int gtid = b * CHOL_THREADS + tid, gthreads = CHOL_CL * CHOL_THREADS;
-  const int64_t kk = (int64_t)k * k;
+  constexpr int SLOTS = chol_slots<CL>();
+  const int gtid = b * CHOL_THREADS + tid, gthreads = CL * CHOL_THREADS;
+  // Whole-matrix passes: a row per warp, columns over the lanes (no index divisions).
+  const int lane = tid & 31, nw = CHOL_THREADS / 32, gwarp = b * nw + (tid >> 5);
   {
     if (tid == 0) fmax_s = 0ull;
     __syncthreads();
     unsigned long long mb = 0ull;
-    for (int64_t t = tid; t < kk; t += CHOL_THREADS) {
-      const int r = (int)(t / k), c = (int)(t % k);
-      if (c < r) continue;
-      const double f = G[t] - (c == r ? 1.0 : 0.0);
-      const unsigned long long bb =
-          (unsigned long long)__double_as_longlong(f) & 0x7fffffffffffffffull;
-      mb = bb > mb ? bb : mb;
+    for (int r = tid >> 5; r < k; r += nw) {
+      const double* Gr = G + (int64_t)r * k;
+      for (int c = r + lane; c < k; c += 32) {
+        double f = Gr[c];
+        if (c == r) f -= 1.0;  // the only FP64 operation of the test
+        const unsigned long long bb =
+            (unsigned long long)__double_as_longlong(f) & 0x7fffffffffffffffull;
+        mb = bb > mb ? bb : mb;
+      }
     }
     atomicMax(&fmax_s, mb);
     __syncthreads();
     if (__longlong_as_double((long long)fmax_s) <= 7.450580596923828e-9) {
-      for (int64_t t = gtid; t < kk; t += gthreads) {
-        const int r = (int)(t / k), c = (int)(t % k);
-        const double drr = 0.5 * (1.0 + G[(int64_t)r * k + r]);
-        W[t] = c > r ? G[t] : (c == r ? drr : 0.0);
-        if (c == r) rdinv[r] = 1.0 / drr;
+      for (int r = gwarp; r < k; r += CL * nw) {
+        const double* Gr = G + (int64_t)r * k;
+        double* Wr = W + (int64_t)r * k;
+        for (int c = lane; c < k; c += 32) {
+          double v = c > r ? Gr[c] : 0.0;
+          if (c == r) {
+            v = 0.5 * (1.0 + Gr[c]);
+            rdinv[r] = 1.0 / v;
+          }
+          Wr[c] = v;
+        }
       }
       return;  // uniform over the cluster: every CTA read the same G
     }
@@ -437,22 +456,27 @@ chol_cluster_kernel(const double* __restrict__ G, int k, int64_t nrows, double* 
     }
     __syncthreads();
     const double shift = shift_s;
-    for (int64_t t = gtid; t < kk; t += gthreads) {
-      const int r = (int)(t / k), c = (int)(t % k);
-      W[t] = c >= r ? G[t] + (c == r ? shift : 0.0) : 0.0;
+    for (int r = gwarp; r < k; r += CL * nw) {
+      const double* Gr = G + (int64_t)r * k;
+      double* Wr = W + (int64_t)r * k;
+      for (int c = lane; c < k; c += 32) {
+        double v = c >= r ? Gr[c] : 0.0;
+        if (c == r && attempt == 1) v += shift;
+        Wr[c] = v;
+      }
     }
     cluster_round_barrier();
     bool bad = false;
     for (int J0 = 0; J0 < k; J0 += CHOL_NB) {
       const int jb = min(CHOL_NB, k - J0), J1 = J0 + jb, m = k - J1;
-      const int nc = m > b ? (m - b + CHOL_CL - 1) / CHOL_CL : 0;
+      const int nc = m > b ? (m - b + CL - 1) / CL : 0;
       const int nelem = jb * nc + jb * (jb + 1) / 2;
       // This thread's elements of the block row: row r, rowbuf slot x (x < CHOL_NB: diagonal
-      // column J0 + x; otherwise panel column J1 + b + CHOL_CL (x - CHOL_NB)).
-      int er[CHOL_SLOTS], ex[CHOL_SLOTS];
-      double a[CHOL_SLOTS];
+      // column J0 + x; otherwise panel column J1 + b + CL (x - CHOL_NB)).
+      int er[SLOTS], ex[SLOTS];
+      double a[SLOTS];
 #pragma unroll
-      for (int e = 0; e < CHOL_SLOTS; ++e) {
+      for (int e = 0; e < SLOTS; ++e) {
         const int idx = tid + e * CHOL_THREADS;
         er[e] = -1;
         ex[e] = 0;
@@ -468,7 +492,7 @@ chol_cluster_kernel(const double* __restrict__ G, int k, int64_t nrows, double* 
             }
             rem -= len;
           }
-          const int col = ex[e] < CHOL_NB ? J0 + ex[e] : J1 + b + CHOL_CL * (ex[e] - CHOL_NB);
+          const int col = ex[e] < CHOL_NB ? J0 + ex[e] : J1 + b + CL * (ex[e] - CHOL_NB);
           a[e] = __ldcg(W + (int64_t)(J0 + er[e]) * k + col);
           if (er[e] == 0) {
             rowbuf[0][ex[e]] = a[e];
@@ -481,14 +505,13 @@ chol_cluster_kernel(const double* __restrict__ G, int k, int64_t nrows, double* 
       }
       for (int j = 0; j < jb; ++j) {
         __syncthreads();
-        const double d = rowbuf[j & 1][j];
-        if (!(d > 0.0)) {  // every thread of every CTA reads the same pivot
+        if (!positive_f64(rowbuf[j & 1][j])) {  // every thread of every CTA reads the same pivot
           bad = true;
           break;
         }
         const double dinv = dinv_s[j & 1];
 #pragma unroll
-        for (int e = 0; e < CHOL_SLOTS; ++e) {
+        for (int e = 0; e < SLOTS; ++e) {
           if (er[e] > j) {
             const double f = rowbuf[j & 1][er[e]] * dinv;
             a[e] = fma(-f, rowbuf[j & 1][ex[e]], a[e]);
@@ -507,11 +530,11 @@ chol_cluster_kernel(const double* __restrict__ G, int k, int64_t nrows, double* 
       if (tid < jb) ri_s[tid] = rsqrt(piv_s[tid]);
       __syncthreads();
 #pragma unroll
-      for (int e = 0; e < CHOL_SLOTS; ++e) {
+      for (int e = 0; e < SLOTS; ++e) {
         if (er[e] >= 0) {
           a[e] *= ri_s[er[e]];
           if (ex[e] >= CHOL_NB)
-            W[(int64_t)(J0 + er[e]) * k + J1 + b + CHOL_CL * (ex[e] - CHOL_NB)] = a[e];
+            W[(int64_t)(J0 + er[e]) * k + J1 + b + CL * (ex[e] - CHOL_NB)] = a[e];
         }
       }
       if (b == 0 && tid < jb) rdinv[J0 + tid] = ri_s[tid];
@@ -522,7 +545,7 @@ chol_cluster_kernel(const double* __restrict__ G, int k, int64_t nrows, double* 
       }
       if (b == 0) {
 #pragma unroll
-        for (int e = 0; e < CHOL_SLOTS; ++e)
+        for (int e = 0; e < SLOTS; ++e)
           if (er[e] >= 0 && ex[e] < CHOL_NB) W[(int64_t)(J0 + er[e]) * k + J0 + ex[e]] = a[e];
       }
       __syncthreads();
@@ -958,6 +981,44 @@ int cholqr_pass_inverse(EigOps& e, double* V, int64_t ldv, int n, int k, const C
   return TUCKER_OK;
 }
 
+// Launch shape of chol_cluster_kernel<cl> (cluster dimension attached by the caller).
+cudaLaunchConfig_t chol_launch_config(int cl, int k, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl, 1, 1);
+  cfg.blockDim = dim3(CHOL_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = sizeof(double) * CHOL_NB * (size_t)std::max(k - 1, 1);
+  cfg.stream = s;
+  return cfg;
+}
+
+// Cluster size of the Cholesky: 16 CTAs (a non-portable size) when the GPU reports that such a
+// cluster of this kernel fits, else the portable 8; 0 when neither can be configured.
+int chol_cluster_size() {
+  const int max_smem = (int)(sizeof(double) * CHOL_NB * (TRSM_MAX_K - 1));
+  if (cudaFuncSetAttribute(chol_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           max_smem) != cudaSuccess)
+    return 0;
+  if (cudaFuncSetAttribute(chol_cluster_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           max_smem) == cudaSuccess &&
+      cudaFuncSetAttribute(chol_cluster_kernel<16>,
+                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = chol_launch_config(16, TRSM_MAX_K, nullptr);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, chol_cluster_kernel<16>, &cfg) == cudaSuccess &&
+        clusters >= 1)
+      return 16;
+  }
+  (void)cudaGetLastError();  // a refused non-portable size leaves no sticky error
+  return 8;
+}
+
 // One pass for k <= TRSM_MAX_K, all on the device: G = V^T V, R = chol(G) (shifted on
 // breakdown, flagged in *stat), V <- V R^{-1} by row-wise triangular solves.
 int cholqr_pass(EigOps& e, double* V, int64_t ldv, int n, int k, const CholWork& w, int* stat,
@@ -965,24 +1026,22 @@ int cholqr_pass(EigOps& e, double* V, int64_t ldv, int n, int k, const CholWork&
   TK_TRY(op_tn(e, k, k, n, V, ldv, V, ldv, w.Gk, k));
   {
     ProfScope prof("chol_f64", s, (double)k * k * k / 3.0, 0.0);
-    constexpr int max_smem = (int)(sizeof(double) * CHOL_NB * (TRSM_MAX_K - 1));
-    static const cudaError_t attr = cudaFuncSetAttribute(
-        chol_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    TK_CUDA(attr);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(CHOL_CL, 1, 1);
-    cfg.blockDim = dim3(CHOL_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = sizeof(double) * CHOL_NB * (size_t)std::max(k - 1, 1);
-    cfg.stream = s;
-    cudaLaunchAttribute cl[1];
-    cl[0].id = cudaLaunchAttributeClusterDimension;
-    cl[0].val.clusterDim.x = CHOL_CL;
-    cl[0].val.clusterDim.y = 1;
-    cl[0].val.clusterDim.z = 1;
-    cfg.attrs = cl;
+    static const int cl = chol_cluster_size();
+    TK_CUDA(cl > 0 ? cudaSuccess : cudaErrorLaunchOutOfResources);
+    cudaLaunchConfig_t cfg = chol_launch_config(cl, k, s);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
     cfg.numAttrs = 1;
-    TK_CUDA(cudaLaunchKernelEx(&cfg, chol_cluster_kernel, (const double*)w.Gk, k, (int64_t)n,
-                               w.R, w.rd, stat));
+    if (cl == 16)
+      TK_CUDA(cudaLaunchKernelEx(&cfg, chol_cluster_kernel<16>, (const double*)w.Gk, k,
+                                 (int64_t)n, w.R, w.rd, stat));
+    else
+      TK_CUDA(cudaLaunchKernelEx(&cfg, chol_cluster_kernel<8>, (const double*)w.Gk, k,
+                                 (int64_t)n, w.R, w.rd, stat));
   }
   TK_LAUNCH();
   return trsm_rows(V, ldv, n, k, w.R, w.rd, stat, s);
