@@ -25,8 +25,7 @@ def ragged(tucker_lib):
     return X, T
 
 
-def test_orderings_bit_exact(tucker_lib, ragged):
-    X, T = ragged
+def check_orderings(tucker_lib, X, T):
     for order in itertools.permutations(range(3)):
         g = tucker_lib.tucker_ordering(T, *order)
         r = O.csf_ordering(X.dims, X.idx, X.val, order)
@@ -36,6 +35,20 @@ def test_orderings_bit_exact(tucker_lib, ragged):
         np.testing.assert_array_equal(g["fiber_ptr"], r["fiber_ptr"])
         np.testing.assert_array_equal(g["leaf_idx"], r["leaf_idx"])
         assert g["val"].tobytes() == r["val"].tobytes()
+
+
+def test_orderings_bit_exact(tucker_lib, ragged):
+    X, T = ragged
+    check_orderings(tucker_lib, X, T)
+
+
+@pytest.mark.parametrize("dims,nnz", [((64, 64, 32), 30000), ((256, 256, 512), 40000)])
+def test_orderings_bit_exact_nine_bit_pass(tucker_lib, dims, nnz):
+    """Keys of 17 and 25 bits: the radix sort's last pass takes 9 bits (as it does for the
+    33-bit keys of a 2000^3 tensor), both in the canonical sort and in every ordering."""
+    X = synth.random_sparse_tensor(dims, nnz, 211)
+    T = tucker_lib.tucker_tensor_create(X.idx, X.val, X.dims)
+    check_orderings(tucker_lib, X, T)
 
 
 def test_duplicates_and_device_input(tucker_lib):
@@ -109,7 +122,12 @@ def spiked_psd(n, J, seed, gap=0.5):
     return (Q * w) @ Q.T
 
 
-@pytest.mark.parametrize("n,J", [(100, 10), (157, 60), (400, 20), (700, 50)])
+# (100, 10) and (157, 60) solve all eigenpairs at once; the others run the subspace iteration
+# with blocks of k = J + max(16, J / 2) = 36, 75, 300 and 384 columns, whose Cholesky-QR
+# factorisations take 3, 5, 19 and 24 block rows of 16 (384 is the largest the cluster
+# factorisation takes)
+@pytest.mark.parametrize("n,J", [(100, 10), (157, 60), (400, 20), (700, 50), (1000, 200),
+                                 (1000, 256)])
 def test_eig_topk(tucker_lib, n, J):
     M = spiked_psd(n, J, 500 + n)
     U, lam = tucker_lib.tucker_eig_topk(M, J)
