@@ -121,41 +121,48 @@ int exclusive_scan(const T* in, T* out, int64_t n, T* d_total, cudaStream_t s) {
   return TUCKER_OK;
 }
 
-// ---- stable LSD radix sort of (64-bit key, 32-bit value) pairs, 8 bits per pass ------------
+// ---- stable LSD radix sort of (64-bit key, 32-bit value) pairs ------------------------------
+// Digits of RB bits: 8 per pass, except that a key whose width leaves 9 bits for the last pass
+// takes them in one 9-bit pass (33-bit keys of 2000^3 tensors: 4 passes instead of 5).
+template <int RB>
 __global__ void rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
                         unsigned* __restrict__ counts, int nblocks) {
-  __shared__ unsigned h[256];
-  h[threadIdx.x] = 0;
+  constexpr int B = 1 << RB;
+  __shared__ unsigned h[B];
+  for (int d = threadIdx.x; d < B; d += THREADS) h[d] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * TILE;
 #pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
     const int64_t i = base + r * THREADS + threadIdx.x;
-    if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 255u], 1u);
+    if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & (B - 1u)], 1u);
   }
   __syncthreads();
-  counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+  for (int d = threadIdx.x; d < B; d += THREADS) counts[(int64_t)d * nblocks + blockIdx.x] = h[d];
 }
 
 // Scatter one tile; an element's destination is the global offset of its digit for this tile
 // plus its rank among equal digits earlier in the tile, so equal digits keep their order.
+template <int RB>
 __global__ void rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                            int64_t n, int shift, const unsigned* __restrict__ offsets,
                            int nblocks, uint64_t* __restrict__ kout,
                            uint32_t* __restrict__ vout) {
-  __shared__ unsigned run[256];
-  __shared__ unsigned wcnt[THREADS / 32][256];
+  constexpr int B = 1 << RB;
+  __shared__ unsigned run[B];
+  __shared__ unsigned wcnt[THREADS / 32][B];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  run[threadIdx.x] = 0;
+  for (int d = threadIdx.x; d < B; d += THREADS) run[d] = 0;
   const int64_t base = (int64_t)blockIdx.x * TILE;
   for (int r = 0; r < ITEMS; ++r) {
 #pragma unroll
-    for (int j = 0; j < THREADS / 32; ++j) wcnt[j][threadIdx.x] = 0;
+    for (int j = 0; j < THREADS / 32; ++j)
+      for (int d = threadIdx.x; d < B; d += THREADS) wcnt[j][d] = 0;
     __syncthreads();
     const int64_t i = base + r * THREADS + threadIdx.x;
     const bool valid = i < n;
     const uint64_t k = valid ? kin[i] : 0ull;
-    const unsigned d = valid ? ((unsigned)(k >> shift) & 255u) : 256u;
+    const unsigned d = valid ? ((unsigned)(k >> shift) & (B - 1u)) : (unsigned)B;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int leader = __ffs(peers) - 1;
     const unsigned rank = __popc(peers & ((1u << lane) - 1u));
@@ -169,12 +176,25 @@ __global__ void rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __r
       vout[dest] = vin[i];
     }
     __syncthreads();
-    unsigned tot = 0;
+    for (int dd = threadIdx.x; dd < B; dd += THREADS) {
+      unsigned tot = 0;
 #pragma unroll
-    for (int j = 0; j < THREADS / 32; ++j) tot += wcnt[j][threadIdx.x];
-    run[threadIdx.x] += tot;
+      for (int j = 0; j < THREADS / 32; ++j) tot += wcnt[j][dd];
+      run[dd] += tot;
+    }
     __syncthreads();
   }
+}
+
+template <int RB>
+int radix_pass(const uint64_t* ki, const uint32_t* vi, uint64_t* ko, uint32_t* vo, int64_t n,
+               int shift, unsigned* counts, int nb, cudaStream_t s) {
+  rs_hist<RB><<<nb, THREADS, 0, s>>>(ki, n, shift, counts, nb);
+  TK_LAUNCH();
+  TK_TRY(exclusive_scan<unsigned>(counts, counts, (int64_t)(1 << RB) * nb, nullptr, s));
+  rs_scatter<RB><<<nb, THREADS, 0, s>>>(ki, vi, n, shift, counts, nb, ko, vo);
+  TK_LAUNCH();
+  return TUCKER_OK;
 }
 
 // Sorts (keys, vals) by the low `bits` bits of the keys.  On return *out_keys/*out_vals point
@@ -186,16 +206,16 @@ int radix_sort_pairs(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1, int
   if (n <= 1) return TUCKER_OK;
   const int nb = ceil_div(n, TILE);
   Buf counts;
-  TK_TRY(counts.alloc(sizeof(unsigned) * 256 * (size_t)nb, s));
+  TK_TRY(counts.alloc(sizeof(unsigned) * 512 * (size_t)nb, s));
   uint64_t *ki = k0, *ko = k1;
   uint32_t *vi = v0, *vo = v1;
-  for (int shift = 0; shift < bits; shift += 8) {
-    rs_hist<<<nb, THREADS, 0, s>>>(ki, n, shift, counts.as<unsigned>(), nb);
-    TK_LAUNCH();
-    TK_TRY(exclusive_scan<unsigned>(counts.as<unsigned>(), counts.as<unsigned>(),
-                                    (int64_t)256 * nb, nullptr, s));
-    rs_scatter<<<nb, THREADS, 0, s>>>(ki, vi, n, shift, counts.as<unsigned>(), nb, ko, vo);
-    TK_LAUNCH();
+  for (int shift = 0; shift < bits;) {
+    const int rb = bits - shift == 9 ? 9 : 8;
+    if (rb == 9)
+      TK_TRY(radix_pass<9>(ki, vi, ko, vo, n, shift, counts.as<unsigned>(), nb, s));
+    else
+      TK_TRY(radix_pass<8>(ki, vi, ko, vo, n, shift, counts.as<unsigned>(), nb, s));
+    shift += rb;
     uint64_t* tk_ = ki; ki = ko; ko = tk_;
     uint32_t* tv_ = vi; vi = vo; vo = tv_;
   }
@@ -408,12 +428,18 @@ int build_ordering(tucker_tensor_s* X, Ordering* ord, cudaStream_t s) {
   const int64_t nnz = X->nnz;
   const int64_t dn = X->dims[n], dm = X->dims[m], dd = X->dims[o];
   ProfScope prof("csf_build", s, 0.0, 20.0 * nnz + 12.0 * nnz);
+  // The canonical COO is sorted by (i_0, i_1, i_2) with distinct keys (build_canonical), so
+  // ordering (0, 1, 2) is already in key order: its stable sort is the identity permutation
+  // that make_keys writes, and no radix pass runs.
+  const bool presorted = n == 0 && m == 1 && o == 2;
   Buf k0, k1, v0, v1, head, fid, tot;
   const size_t nn = (size_t)(nnz ? nnz : 1);
   TK_TRY(k0.alloc(8 * nn, s));
-  TK_TRY(k1.alloc(8 * nn, s));
   TK_TRY(v0.alloc(4 * nn, s));
-  TK_TRY(v1.alloc(4 * nn, s));
+  if (!presorted) {
+    TK_TRY(k1.alloc(8 * nn, s));
+    TK_TRY(v1.alloc(4 * nn, s));
+  }
   TK_TRY(head.alloc(4 * nn, s));
   TK_TRY(fid.alloc(4 * nn, s));
   TK_TRY(tot.alloc(sizeof(unsigned), s));
@@ -423,11 +449,12 @@ int build_ordering(tucker_tensor_s* X, Ordering* ord, cudaStream_t s) {
                                   k0.as<uint64_t>(), v0.as<uint32_t>());
     TK_LAUNCH();
   }
-  uint64_t* keys;
-  uint32_t* perm;
-  TK_TRY(radix_sort_pairs(k0.as<uint64_t>(), v0.as<uint32_t>(), k1.as<uint64_t>(),
-                          v1.as<uint32_t>(), nnz, key_bits((uint64_t)dn * dm * dd - 1), &keys,
-                          &perm, s));
+  uint64_t* keys = k0.as<uint64_t>();
+  uint32_t* perm = v0.as<uint32_t>();
+  if (!presorted)
+    TK_TRY(radix_sort_pairs(k0.as<uint64_t>(), v0.as<uint32_t>(), k1.as<uint64_t>(),
+                            v1.as<uint32_t>(), nnz, key_bits((uint64_t)dn * dm * dd - 1), &keys,
+                            &perm, s));
   TK_CUDA(cudaMalloc(&ord->leaf_idx, sizeof(int32_t) * nn));
   TK_CUDA(cudaMalloc(&ord->val, sizeof(double) * nn));
   unsigned F = 0;
