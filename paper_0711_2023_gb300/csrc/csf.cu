@@ -141,19 +141,53 @@ __global__ void rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
   for (int d = threadIdx.x; d < B; d += THREADS) counts[(int64_t)d * nblocks + blockIdx.x] = h[d];
 }
 
-// Scatter one tile; an element's destination is the global offset of its digit for this tile
-// plus its rank among equal digits earlier in the tile, so equal digits keep their order.
+// Scatter one tile.  An element's destination is the global offset of its digit for this tile
+// plus its rank among equal digits earlier in the tile, so equal digits keep their order.  The
+// tile is first placed in shared memory grouped by digit (tile-local offsets from its own
+// histogram), then written out in that order: each digit's elements leave as one contiguous run
+// instead of one scattered store per element.
 template <int RB>
-__global__ void rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                           int64_t n, int shift, const unsigned* __restrict__ offsets,
-                           int nblocks, uint64_t* __restrict__ kout,
-                           uint32_t* __restrict__ vout) {
+__global__ void __launch_bounds__(THREADS)
+rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n,
+           int shift, const unsigned* __restrict__ offsets, int nblocks,
+           uint64_t* __restrict__ kout, uint32_t* __restrict__ vout) {
   constexpr int B = 1 << RB;
-  __shared__ unsigned run[B];
+  constexpr int DPT = B / THREADS;  // digits per thread in the tile-local scan
+  static_assert(B % THREADS == 0, "digit count must be a multiple of the block size");
+  __shared__ unsigned run[B];   // the tile's histogram, then elements of each digit placed so far
+  __shared__ unsigned loc[B];   // tile-local start of each digit's run
   __shared__ unsigned wcnt[THREADS / 32][B];
+  __shared__ uint64_t sk[TILE];
+  __shared__ uint32_t sv[TILE];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int d = threadIdx.x; d < B; d += THREADS) run[d] = 0;
   const int64_t base = (int64_t)blockIdx.x * TILE;
+  for (int d = threadIdx.x; d < B; d += THREADS) run[d] = 0;
+  __syncthreads();
+  uint64_t kr[ITEMS];
+#pragma unroll
+  for (int r = 0; r < ITEMS; ++r) {
+    const int64_t i = base + r * THREADS + threadIdx.x;
+    kr[r] = i < n ? kin[i] : 0ull;
+    if (i < n) atomicAdd(&run[(unsigned)(kr[r] >> shift) & (B - 1u)], 1u);
+  }
+  __syncthreads();
+  {
+    unsigned c[DPT], t = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      c[q] = run[threadIdx.x * DPT + q];
+      t += c[q];
+    }
+    unsigned ex = block_exclusive_scan<unsigned>(t, nullptr);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      loc[threadIdx.x * DPT + q] = ex;
+      ex += c[q];
+    }
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < B; d += THREADS) run[d] = 0;
+#pragma unroll
   for (int r = 0; r < ITEMS; ++r) {
 #pragma unroll
     for (int j = 0; j < THREADS / 32; ++j)
@@ -161,7 +195,7 @@ __global__ void rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __r
     __syncthreads();
     const int64_t i = base + r * THREADS + threadIdx.x;
     const bool valid = i < n;
-    const uint64_t k = valid ? kin[i] : 0ull;
+    const uint64_t k = kr[r];
     const unsigned d = valid ? ((unsigned)(k >> shift) & (B - 1u)) : (unsigned)B;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int leader = __ffs(peers) - 1;
@@ -171,9 +205,8 @@ __global__ void rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __r
     if (valid) {
       unsigned pos = run[d] + rank;
       for (int j = 0; j < w; ++j) pos += wcnt[j][d];
-      const unsigned dest = offsets[(int64_t)d * nblocks + blockIdx.x] + pos;
-      kout[dest] = k;
-      vout[dest] = vin[i];
+      sk[loc[d] + pos] = k;
+      sv[loc[d] + pos] = vin[i];
     }
     __syncthreads();
     for (int dd = threadIdx.x; dd < B; dd += THREADS) {
@@ -183,6 +216,14 @@ __global__ void rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __r
       run[dd] += tot;
     }
     __syncthreads();
+  }
+  const int cnt = (int)(n - base < (int64_t)TILE ? n - base : (int64_t)TILE);
+  for (int j = threadIdx.x; j < cnt; j += THREADS) {
+    const uint64_t k = sk[j];
+    const unsigned d = (unsigned)(k >> shift) & (B - 1u);
+    const unsigned dest = offsets[(int64_t)d * nblocks + blockIdx.x] + (unsigned)j - loc[d];
+    kout[dest] = k;
+    vout[dest] = sv[j];
   }
 }
 

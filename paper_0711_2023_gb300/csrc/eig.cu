@@ -346,11 +346,11 @@ chol_inv_kernel(const double* __restrict__ G, int k, double shift, double* __res
 // (G = I + F; exact to O(|F|^2) < eps) with no serial factorisation.
 //   Otherwise right-looking by blocks of CHOL_NB rows.  For block row J (rows J0..J1-1):
 //   1. every CTA factors the diagonal block and its own share of the panel columns (columns
-//      J1 + b + CL s for CTA b), one element of the block row per thread, by jb unscaled
+//      J1 + b + CL s for CTA b), one or two elements of the block row per thread, by jb unscaled
 //      elimination steps a[r][c] -= a[j][r] a[j][c] / d_j; the diagonal block is factored
 //      redundantly by every CTA from identical data, so all CTAs take the same branches.  Row j+1
 //      is published in shared memory as soon as step j has finished it; the thread holding the
-//      next pivot forms its reciprocal (recip_newton).  The rows are then scaled by
+//      next pivot forms its reciprocal (pivot_recip).  The rows are then scaled by
 //      1 / sqrt(d_r) and the panel written back;
 //   2. after a cluster barrier every CTA reads the whole panel P (jb x m) and the trailing upper
 //      triangle takes W[q][c] -= sum_i P[i][q] P[i][c], its elements spread over all threads of
@@ -381,7 +381,7 @@ __device__ __forceinline__ bool positive_f64(double d) {
 // third-order step x <- x (1 + e + e^2) with e = 1 - d x, which cubes the relative error (the
 // Newton-Raphson step x (1 + e) only squares it), to FP64 rounding level in three dependent FMAs.
 // Exponents outside [1, 2044] take the division.
-__device__ __forceinline__ double recip_newton(double d) {
+__device__ __forceinline__ double pivot_recip(double d) {
   const long long bits = __double_as_longlong(d);
   const int e = (int)((bits >> 52) & 0x7ff);
   if (e < 1 || e > 2044) return 1.0 / d;
@@ -498,7 +498,7 @@ chol_cluster_kernel(const double* __restrict__ G, int k, int64_t nrows, double* 
             rowbuf[0][ex[e]] = a[e];
             if (ex[e] == 0) {
               piv_s[0] = a[e];
-              dinv_s[0] = recip_newton(a[e]);
+              dinv_s[0] = pivot_recip(a[e]);
             }
           }
         }
@@ -519,7 +519,7 @@ chol_cluster_kernel(const double* __restrict__ G, int k, int64_t nrows, double* 
               rowbuf[(j + 1) & 1][ex[e]] = a[e];
               if (ex[e] == j + 1) {
                 piv_s[j + 1] = a[e];
-                dinv_s[(j + 1) & 1] = recip_newton(a[e]);
+                dinv_s[(j + 1) & 1] = pivot_recip(a[e]);
               }
             }
           }
