@@ -15,9 +15,9 @@
 //         block stays well conditioned, two filter applications per Rayleigh-Ritz step (four
 //         power steps while an outlier eigenvalue pins d to 1); optionally the filter's
 //         products run in FP32 until the residuals near the FP32 noise floor;
-//       - Cholesky-QR2 orthonormalisation in FP64 (R = chol(V^T V), then x R = v solved for
-//         every row v of V, twice), with a shifted pass when the Gram matrix is not
-//         numerically positive definite.
+//       - Cholesky-QR2 orthonormalisation in FP64 (R = chol(V^T V), factored by blocks over one
+//         thread-block cluster, then x R = v solved for every row v of V, twice), with a
+//         shifted pass when the Gram matrix is not numerically positive definite.
 //   The returned columns are sorted by eigenvalue (largest first) and sign-normalised: the
 //   entry of largest magnitude in each column is positive.
 #include <math.h>
